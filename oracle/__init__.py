@@ -1,0 +1,202 @@
+"""Plain FP64 CPU oracle for the DE phase-tracking hot path (arxiv 1906.10598).
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg may import this package. The CUDA
+library never imports, links or calls it, and it never touches the CUDA path.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, libm ``cos``); this module
+builds it with gcc and exposes numpy-friendly wrappers:
+
+* ``sse`` / ``sse_many``  -- chi-square objective, Sec. 2.2 Eq. 2-2-4 with the
+  model of Eq. 2-2-2 (c5 = 0) written in cycles.
+* ``de_solve``            -- DE/rand/1/bin with the Table 3-1-1 controls.
+* ``de_textbook``         -- the same DE on sphere / Rosenbrock (self-check).
+* ``philox4x32_10``       -- Salmon et al. SC'11 counter-based generator.
+* ``theta_to_c``, ``c_phase``, ``c_freq``, ``c_total_phase`` -- Eq. 3-1-1 and
+  Eq. 4-1-2 observables in the paper's c0..c3 coefficients.
+* ``crb``                 -- Cramer-Rao bound from the exact Fisher matrix of
+  the model (textbook estimation theory; the paper gives none).
+
+Parity status: every function above is pinned by a ``-m "not gpu"`` test
+against something other than itself (closed forms, identities, brute force,
+published known answers, the paper's Appendix 1 example).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+D = 5
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, -O2, OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        lib.oc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        lib.oc_philox4x32_10.restype = None
+        lib.oc_phase_cycles.argtypes = [dp, ctypes.c_double]
+        lib.oc_phase_cycles.restype = ctypes.c_double
+        lib.oc_model.argtypes = [dp, ctypes.c_double]
+        lib.oc_model.restype = ctypes.c_double
+        lib.oc_sse.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp]
+        lib.oc_sse.restype = ctypes.c_double
+        lib.oc_sse_many.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int64, dp,
+                                    ctypes.c_int]
+        lib.oc_sse_many.restype = None
+        lib.oc_de_solve_block.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                          ctypes.c_uint32, dp, dp, dp, ctypes.c_int]
+        lib.oc_de_solve_block.restype = ctypes.c_int
+        lib.oc_de_textbook.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_uint64, dp]
+        lib.oc_de_textbook.restype = ctypes.c_int
+        for name in ("oc_c_phase", "oc_c_freq", "oc_c_total_phase"):
+            fn = getattr(lib, name)
+            fn.argtypes = [dp, ctypes.c_double]
+            fn.restype = ctypes.c_double
+        lib.oc_theta_to_c.argtypes = [dp, dp]
+        lib.oc_theta_to_c.restype = None
+        _lib = lib
+        return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def philox4x32_10(counter, key) -> np.ndarray:
+    """One Philox4x32-10 block: 4 uint32 words for a 4-word counter, 2-word key."""
+    lib = _load()
+    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    p = ctypes.POINTER(ctypes.c_uint32)
+    lib.oc_philox4x32_10(c.ctypes.data_as(p), k.ctypes.data_as(p), out.ctypes.data_as(p))
+    return out
+
+
+def phase_cycles(theta, t: float) -> float:
+    """p(t) = phi0/(2 pi) + f0 t + f1 t^2/2 + f2 t^3/6 (cycles)."""
+    th = _f64(theta)
+    return _load().oc_phase_cycles(_dptr(th), float(t))
+
+
+def model(theta, t: float) -> float:
+    th = _f64(theta)
+    return _load().oc_model(_dptr(th), float(t))
+
+
+def sse(samples, fs: float, t0: float, theta) -> float:
+    """Eq. 2-2-4 objective of one candidate theta = (A, phi0, f0, f1, f2)."""
+    s = _f64(samples)
+    th = _f64(theta)
+    return _load().oc_sse(_dptr(s), s.size, float(fs), float(t0), _dptr(th))
+
+
+def sse_many(samples, fs: float, t0: float, cands, nthreads: int = 0) -> np.ndarray:
+    """Eq. 2-2-4 objective for each row of ``cands`` (n x 5); OpenMP over rows."""
+    s = _f64(samples)
+    c = _f64(cands).reshape(-1, D)
+    out = np.zeros(c.shape[0], dtype=np.float64)
+    _load().oc_sse_many(_dptr(s), s.size, float(fs), float(t0), _dptr(c), c.shape[0], _dptr(out), int(nthreads))
+    return out
+
+
+def de_solve(samples, fs: float, t0: float, bounds, pop: int, gens: int, F: float, CR: float, seed: int,
+             block_id: int = 0, nthreads: int = 0, return_population: bool = False):
+    """DE/rand/1/bin fit of one block. Returns (params[5], sse) or, with
+    ``return_population``, (params, sse, population[pop,5], fitness[pop])."""
+    s = _f64(samples)
+    b = _f64(bounds).reshape(D, 2)
+    out = np.zeros(D + 1, dtype=np.float64)
+    popv = np.zeros((pop, D), dtype=np.float64)
+    fit = np.zeros(pop, dtype=np.float64)
+    rc = _load().oc_de_solve_block(_dptr(s), s.size, float(fs), float(t0), _dptr(b), int(pop), int(gens), float(F),
+                                   float(CR), ctypes.c_uint64(int(seed)), ctypes.c_uint32(int(block_id)), _dptr(out),
+                                   _dptr(popv), _dptr(fit), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle de_solve: invalid arguments")
+    if return_population:
+        return out[:D].copy(), float(out[D]), popv, fit
+    return out[:D].copy(), float(out[D])
+
+
+def de_textbook(which: str, bounds, pop: int, gens: int, F: float, CR: float, seed: int):
+    """The oracle's DE on a 5-D textbook function ('sphere' or 'rosenbrock')."""
+    b = _f64(bounds).reshape(D, 2)
+    out = np.zeros(D + 1, dtype=np.float64)
+    rc = _load().oc_de_textbook(0 if which == "sphere" else 1, _dptr(b), int(pop), int(gens), float(F), float(CR),
+                                ctypes.c_uint64(int(seed)), _dptr(out))
+    if rc != 0:
+        raise ValueError("oracle de_textbook: invalid arguments")
+    return out[:D].copy(), float(out[D])
+
+
+def theta_to_c(theta) -> np.ndarray:
+    """(A, phi0, f0, f1, f2) -> paper coefficients (c0, c1, c2, c3, c4), Eq. 2-2-3."""
+    th = _f64(theta)
+    c = np.zeros(5, dtype=np.float64)
+    _load().oc_theta_to_c(_dptr(th), _dptr(c))
+    return c
+
+
+def c_phase(c, t: float) -> float:
+    """Eq. 3-1-1 phase (rad) from c0..c3."""
+    cc = _f64(c)[:4].copy()
+    return _load().oc_c_phase(_dptr(cc), float(t))
+
+
+def c_freq(c, t: float) -> float:
+    """Eq. 3-1-1 instantaneous frequency (rad/s) from c0..c3."""
+    cc = _f64(c)[:4].copy()
+    return _load().oc_c_freq(_dptr(cc), float(t))
+
+
+def c_total_phase(c, T: float) -> float:
+    """Eq. 4-1-2 for a single block of length T: phi(T/2) - phi(-T/2) (rad)."""
+    cc = _f64(c)[:4].copy()
+    return _load().oc_c_total_phase(_dptr(cc), float(T))
+
+
+def crb(theta, n: int, fs: float, t0: float, sigma: float) -> np.ndarray:
+    """Cramer-Rao standard deviations of (A, phi0, f0, f1, f2) for white
+    Gaussian noise of standard deviation ``sigma``: the inverse of the Fisher
+    matrix J = sigma^-2 sum_i grad m(t_i) grad m(t_i)^T at ``theta``, with
+    m = A cos(phi0 + 2 pi (f0 t + f1 t^2/2 + f2 t^3/6)). Textbook result."""
+    A, phi0, f0, f1, f2 = [float(v) for v in theta]
+    t = t0 + np.arange(n, dtype=np.float64) / fs
+    ph = phi0 + 2.0 * np.pi * (f0 * t + f1 * t * t / 2.0 + f2 * t ** 3 / 6.0)
+    c, s = np.cos(ph), np.sin(ph)
+    g = np.stack([c, -A * s, -A * s * 2 * np.pi * t, -A * s * np.pi * t * t, -A * s * np.pi * t ** 3 / 3.0])
+    J = (g @ g.T) / (sigma * sigma)
+    return np.sqrt(np.diag(np.linalg.inv(J)))

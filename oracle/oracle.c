@@ -1,0 +1,303 @@
+/*
+ * Plain FP64 CPU oracle for the DE phase-tracking hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the package smoke check and
+ * the benchmark's CPU-baseline / reference leg may load, call or execute this
+ * code. The CUDA library shares no code with it: nothing here is included,
+ * linked or generated for the GPU path, and nothing here reads the GPU path.
+ *
+ * What it computes (arxiv 1906.10598):
+ *   - Signal model, Sec. 2.2 Eq. 2-2-2 with the amplitude slope c5 = 0 and
+ *     the Taylor phase of Eq. 2-2-1 / Eq. 2-2-3, re-parameterised in cycles:
+ *       m(t) = A cos(2 pi p(t)),  p(t) = phi0/(2 pi) + f0 t + f1 t^2/2 + f2 t^3/6
+ *     i.e. c0 = phi0, c1 = 2 pi f0, c2 = pi f1, c3 = pi f2 / 3, c4 = A.
+ *   - Chi-square objective with unit weights, Sec. 2.2 Eq. 2-2-4:
+ *       F(theta) = sum_i (s_i - m(t_i))^2.
+ *   - Differential Evolution, Sec. 1.2 (mutation -> crossover -> selection,
+ *     Fig. "DE algorithm iteration flowchart") with the controls of Sec. 3.1.2
+ *     Table 3-1-1 (F, CR, fixed itermax as the stop rule).  The mutation
+ *     strategy is DE/rand/1 with binomial crossover; the paper names its
+ *     strategies only by number, so the textbook rand/1/bin form is used.
+ *   - Derived observables: phase and instantaneous frequency, Sec. 3.1.3
+ *     Eq. 3-1-1; block total-count phase, Sec. 4.1.1 Eq. 4-1-2.
+ *   - Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
+ *     "Parallel random numbers: as easy as 1, 2, 3", SC'11), written from
+ *     the published definition.
+ *
+ * Readings where the paper is silent (each restated in the design notes):
+ *   t_i = t0 + i/fs; SSE accumulated in long double in index order; the
+ *   fractional cycle is p - nearbyint(p) before the 2 pi scaling; DE index
+ *   draws use Lemire's multiply-shift on one 32-bit word with index shifting
+ *   (no rejection); crossover compares a raw 32-bit word against
+ *   floor(CR 2^32); out-of-range trial components are pulled to the midpoint
+ *   of the violated bound and the parent's component, except phi0 whose range
+ *   is the full circle, which wraps; selection keeps the trial on ties; the
+ *   final answer is the lowest-index minimum.
+ *
+ * Parity pins live in the test suite (closed-form tone sums, noise-energy
+ * identities, brute-force grids, cuRAND/Random123 known answers, textbook
+ * DE test functions, the paper's Appendix 1 worked example).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OC_D 5
+static const double OC_PI = 3.14159265358979323846264338327950288;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al. SC'11): 10 rounds of a two-multiplier
+ * Feistel-like bijection on a 128-bit counter, keyed by a 64-bit key that is
+ * bumped by the Weyl constants between rounds. */
+static const uint32_t PHILOX_MUL0 = 0xD2511F53u, PHILOX_MUL1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_WEYL0 = 0x9E3779B9u, PHILOX_WEYL1 = 0xBB67AE85u;
+
+void oc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += PHILOX_WEYL0; k1 += PHILOX_WEYL1; }
+    uint64_t p0 = (uint64_t)PHILOX_MUL0 * c0;
+    uint64_t p1 = (uint64_t)PHILOX_MUL1 * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Twelve words for DE draws of individual `ind` at generation `gen` of block
+ * `block_id`: counters (group, ind, gen, block_id) for group = 0, 1, 2. */
+static void oc_draw12(uint64_t seed, uint32_t block_id, uint32_t gen, uint32_t ind, uint32_t w[12]) {
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  for (uint32_t g = 0; g < 3; ++g) {
+    uint32_t ctr[4] = {g, ind, gen, block_id};
+    oc_philox4x32_10(ctr, key, w + 4 * g);
+  }
+}
+
+/* Uniform double in [0,1) with 53 random bits (27 from a, 26 from b). */
+static double oc_u53(uint32_t a, uint32_t b) {
+  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+/* Integer in [0, k) by Lemire's multiply-shift of one 32-bit word. */
+static uint32_t oc_lemire(uint32_t w, uint32_t k) { return (uint32_t)(((uint64_t)w * k) >> 32); }
+
+/* ------------------------------------------------------------------------ */
+/* Model and objective (Eq. 2-2-1..2-2-4, c5 = 0). */
+
+double oc_phase_cycles(const double th[OC_D], double t) {
+  return th[1] / (2.0 * OC_PI) + th[2] * t + th[3] * t * t / 2.0 + th[4] * t * t * t / 6.0;
+}
+
+double oc_model(const double th[OC_D], double t) {
+  double p = oc_phase_cycles(th, t);
+  double r = p - nearbyint(p); /* fractional cycle in [-1/2, 1/2] */
+  return th[0] * cos(2.0 * OC_PI * r);
+}
+
+double oc_sse(const double* s, int64_t n, double fs, double t0, const double th[OC_D]) {
+  long double acc = 0.0L;
+  for (int64_t i = 0; i < n; ++i) {
+    double t = t0 + (double)i / fs;
+    double res = s[i] - oc_model(th, t);
+    acc += (long double)res * (long double)res;
+  }
+  return (double)acc;
+}
+
+/* SSE for `ncand` candidate rows (row-major, 5 per row). */
+void oc_sse_many(const double* s, int64_t n, double fs, double t0, const double* cands, int64_t ncand,
+                 double* out, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int64_t c = 0; c < ncand; ++c) out[c] = oc_sse(s, n, fs, t0, cands + OC_D * c);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Differential Evolution, DE/rand/1/bin, synchronous generations.
+ * The objective is a callback so that the same DE can be checked on textbook
+ * functions; `oc_de_solve_block` binds it to the chi-square objective. */
+
+typedef double (*oc_objective_fn)(const double* th, void* user);
+
+/* The phi0 component (index 1) wraps when its range spans a full circle
+ * (Sec. 3.1.1: the phase range is [0, 2 pi]). */
+static int oc_is_periodic(int j, const double* lo, const double* hi) {
+  return j == 1 && (hi[j] - lo[j]) >= 2.0 * OC_PI * (1.0 - 1e-12);
+}
+
+static double oc_repair(int j, double u, double parent, const double* lo, const double* hi) {
+  if (oc_is_periodic(j, lo, hi)) {
+    double two_pi = 2.0 * OC_PI;
+    double k = floor((u - lo[j]) / two_pi);
+    return u - k * two_pi;
+  }
+  if (u < lo[j]) return (lo[j] + parent) / 2.0;
+  if (u > hi[j]) return (hi[j] + parent) / 2.0;
+  return u;
+}
+
+/* Three distinct indices different from i, drawn without rejection: the
+ * first from NP-1 slots, the second from NP-2, the third from NP-3, each
+ * mapped onto the remaining indices in ascending order. */
+static void oc_pick3(uint32_t i, uint32_t np, const uint32_t w[3], uint32_t r[3]) {
+  uint32_t excl[4];
+  uint32_t nex = 1;
+  excl[0] = i;
+  for (int d = 0; d < 3; ++d) {
+    uint32_t v = oc_lemire(w[d], np - 1 - (uint32_t)d);
+    /* excl is kept sorted ascending */
+    for (uint32_t e = 0; e < nex; ++e)
+      if (v >= excl[e]) v++;
+    r[d] = v;
+    /* insert v into the sorted exclusion list */
+    uint32_t pos = nex;
+    while (pos > 0 && excl[pos - 1] > v) { excl[pos] = excl[pos - 1]; --pos; }
+    excl[pos] = v;
+    nex++;
+  }
+}
+
+/* Runs DE; returns 0 on success, -1 on invalid arguments.
+ * out[0..4] = best vector, out[5] = its objective value.
+ * final_pop (np*5) and final_fit (np) are optional. */
+int oc_de_run(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], int np, int gens, double F,
+              double CR, uint64_t seed, uint32_t block_id, double out[OC_D + 1], double* final_pop,
+              double* final_fit, int nthreads) {
+  if (np < 4 || gens < 0) return -1;
+  double lo[OC_D], hi[OC_D];
+  for (int j = 0; j < OC_D; ++j) {
+    lo[j] = bounds[2 * j];
+    hi[j] = bounds[2 * j + 1];
+    if (!(lo[j] <= hi[j])) return -1;
+  }
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#else
+  (void)nthreads;
+#endif
+  double* x = (double*)malloc(sizeof(double) * np * OC_D);
+  double* fx = (double*)malloc(sizeof(double) * np);
+  double* u = (double*)malloc(sizeof(double) * np * OC_D);
+  double* fu = (double*)malloc(sizeof(double) * np);
+  if (!x || !fx || !u || !fu) { free(x); free(fx); free(u); free(fu); return -1; }
+
+  /* Initial population: uniform inside the bounds (generation index 0). */
+  for (int i = 0; i < np; ++i) {
+    uint32_t w[12];
+    oc_draw12(seed, block_id, 0u, (uint32_t)i, w);
+    for (int j = 0; j < OC_D; ++j) x[i * OC_D + j] = lo[j] + oc_u53(w[2 * j], w[2 * j + 1]) * (hi[j] - lo[j]);
+  }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int i = 0; i < np; ++i) fx[i] = obj(x + i * OC_D, user);
+
+  uint32_t cr_thr = CR >= 1.0 ? 0xffffffffu : (uint32_t)(CR * 4294967296.0);
+  int cr_all = CR >= 1.0;
+  for (int g = 1; g <= gens; ++g) {
+    /* mutation + crossover for every individual, from the generation-(g-1) population */
+    for (int i = 0; i < np; ++i) {
+      uint32_t w[12], r[3];
+      oc_draw12(seed, block_id, (uint32_t)g, (uint32_t)i, w);
+      oc_pick3((uint32_t)i, (uint32_t)np, w, r);
+      uint32_t jrand = oc_lemire(w[3], OC_D);
+      for (int j = 0; j < OC_D; ++j) {
+        double parent = x[i * OC_D + j];
+        int take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
+        double v = x[r[0] * OC_D + j] + F * (x[r[1] * OC_D + j] - x[r[2] * OC_D + j]);
+        u[i * OC_D + j] = take ? oc_repair(j, v, parent, lo, hi) : parent;
+      }
+    }
+    /* evaluate all trials, then select (trial wins ties) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int i = 0; i < np; ++i) fu[i] = obj(u + i * OC_D, user);
+    for (int i = 0; i < np; ++i) {
+      if (fu[i] <= fx[i]) {
+        memcpy(x + i * OC_D, u + i * OC_D, sizeof(double) * OC_D);
+        fx[i] = fu[i];
+      }
+    }
+  }
+  int best = 0;
+  for (int i = 1; i < np; ++i)
+    if (fx[i] < fx[best]) best = i;
+  for (int j = 0; j < OC_D; ++j) out[j] = x[best * OC_D + j];
+  out[OC_D] = fx[best];
+  if (final_pop) memcpy(final_pop, x, sizeof(double) * np * OC_D);
+  if (final_fit) memcpy(final_fit, fx, sizeof(double) * np);
+  free(x); free(fx); free(u); free(fu);
+  return 0;
+}
+
+typedef struct { const double* s; int64_t n; double fs, t0; } oc_block;
+
+static double oc_block_objective(const double* th, void* user) {
+  const oc_block* b = (const oc_block*)user;
+  return oc_sse(b->s, b->n, b->fs, b->t0, th);
+}
+
+int oc_de_solve_block(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_D], int np,
+                      int gens, double F, double CR, uint64_t seed, uint32_t block_id, double out[OC_D + 1],
+                      double* final_pop, double* final_fit, int nthreads) {
+  if (n < 1 || !(fs > 0.0)) return -1;
+  oc_block b = {s, n, fs, t0};
+  return oc_de_run(oc_block_objective, &b, bounds, np, gens, F, CR, seed, block_id, out, final_pop, final_fit,
+                   nthreads);
+}
+
+/* Textbook DE test functions (5-D), for the DE self-check. */
+static double oc_sphere(const double* x, void* user) {
+  (void)user;
+  double s = 0.0;
+  for (int j = 0; j < OC_D; ++j) s += x[j] * x[j];
+  return s;
+}
+static double oc_rosenbrock(const double* x, void* user) {
+  (void)user;
+  double s = 0.0;
+  for (int j = 0; j + 1 < OC_D; ++j) {
+    double a = x[j + 1] - x[j] * x[j], b = 1.0 - x[j];
+    s += 100.0 * a * a + b * b;
+  }
+  return s;
+}
+
+int oc_de_textbook(int which, const double bounds[2 * OC_D], int np, int gens, double F, double CR, uint64_t seed,
+                   double out[OC_D + 1]) {
+  oc_objective_fn f = which == 0 ? oc_sphere : oc_rosenbrock;
+  return oc_de_run(f, NULL, bounds, np, gens, F, CR, seed, 0u, out, NULL, NULL, 1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Observables in the paper's coefficients c0..c3 (radians). */
+
+/* Eq. 3-1-1: phase and instantaneous frequency (rad, rad/s) at t. */
+double oc_c_phase(const double c[4], double t) { return c[0] + c[1] * t + c[2] * t * t + c[3] * t * t * t; }
+double oc_c_freq(const double c[4], double t) { return c[1] + 2.0 * c[2] * t + 3.0 * c[3] * t * t; }
+
+/* Eq. 4-1-2 for one block of length T: phi(T/2) - phi(-T/2). */
+double oc_c_total_phase(const double c[4], double T) { return oc_c_phase(c, T / 2.0) - oc_c_phase(c, -T / 2.0); }
+
+/* theta = (A, phi0, f0, f1, f2) -> c0..c4 (Eq. 2-2-3 in cycles form). */
+void oc_theta_to_c(const double th[OC_D], double c[5]) {
+  c[0] = th[1];
+  c[1] = 2.0 * OC_PI * th[2];
+  c[2] = OC_PI * th[3];
+  c[3] = OC_PI * th[4] / 3.0;
+  c[4] = th[0];
+}
