@@ -1,0 +1,262 @@
+"""Benchmark of the DE phase-tracking hot path (arxiv 1906.10598) on B300.
+
+A step is one full DE fit (DE/rand/1/bin, Table 3-1-1 controls) of the
+paper-size block: N = 400,000 int16 samples at 10 kHz (40 s), population 64,
+1250 generations = 64 x 1251 = 80,064 objective evaluations (the paper's
+400K-sample / ~80,000-evaluation experiment, Sec. 1.3), default precision tier
+(FP64-anchored phase, FP32 cosine and residuals).
+
+Metric: objective sample-evaluations per second = N * pop * (gens + 1) / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this paper
+has) on a bounded sample of the same workload. Under torchrun (N > 1) each
+rank fits its own block (independent blocks: weak scaling, no collective on the
+data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "paper400k_int16_pop64_g1250"
+METRIC = "objective sample-evals/s"
+UNIT = "sample-evals/s"
+# paper: 400K-sample block, ~80,000 objective evaluations, 6.5 s on a GTX580 (Sec. 1.3)
+PAPER_SAMPLE_EVALS_PER_S = 400_000 * 80_000 / 6.5
+# SFU-bound roofline: 148 SMs x 16 cosine ops/clk/SM x 2032 MHz, one cosine per sample-eval
+SMS, SFU_PER_CLK, SM_MAX_MHZ = 148, 16, 2032.0
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm), "sm_mhz_min": float(min(sm))}
+
+
+def cpu_baseline(blk: synth.Block, gens: int = 8):
+    """The oracle (FP64, libm cos, OpenMP over candidates) timed on this host's
+    cores on a bounded sample of the workload: the same block and population
+    for `gens` generations instead of 1250."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    s = blk.values()
+    t = time.perf_counter()
+    oracle.de_solve(s, blk.fs, blk.t0, blk.bounds, blk.pop, gens, blk.F, blk.CR, blk.de_seed, nthreads=cores)
+    dt = time.perf_counter() - t
+    evals = blk.n * blk.pop * (gens + 1)
+    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle DE on the 400K int16 block, pop {blk.pop}, {gens} generations "
+                      f"({evals:.3g} sample-evals, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    blk = synth.paper400k(0)
+    gens = 4
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(blk, gens=gens))
+    timed = vals[args.warmup:]
+    v = float(np.mean([x["value"] for x in timed]))
+    base = dict(timed[-1])
+    base["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": blk.n * blk.pop * (gens + 1) / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": v / PAPER_SAMPLE_EVALS_PER_S, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": blk.n, "fs": blk.fs, "pop": blk.pop, "gens_timed": gens,
+                       "sample": "each step: oracle DE with 4 generations on the full block"},
+            "cpu_baseline": base,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    blk = synth.paper400k(rank)
+    ctx = pt.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream.cuda_stream)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2
+    bounds = blk.bounds
+    evals = blk.sample_evals()
+
+    def step():
+        return ctx.de_solve(bounds, blk.pop, blk.gens, blk.F, blk.CR, blk.de_seed, pt.TIER_F64)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, kern_ms = [], []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        params, sse = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(ctx.last_kernel_ms())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the C ABI with host buffers: H2D of the step's samples
+    # (pt_load_block) + the fit + D2H of the result, every step
+    e2e_s = []
+    for _ in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+        step()
+        e2e_s.append(time.perf_counter() - t)
+    e2e_v = evals / float(np.mean(e2e_s))
+    if world > 1:
+        t = torch.tensor([float(np.mean(e2e_s))], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_v = evals * world / float(t.item())
+
+    value = evals * args.steps * world / (total_ms * 1e-3)
+    k_avg = float(np.mean(kern_ms)) * 1e-3
+    achieved = evals / k_avg
+    peak = SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
+            "traffic": None, "kernel": "k_de<TIER_F64>",
+            "peak_basis": "148 SMs x 16 SFU cosines/clk x 2032 MHz (one cosine per sample-eval)"}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (SMS * SFU_PER_CLK * clocks["sm_mhz"] * 1e6)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / world / PAPER_SAMPLE_EVALS_PER_S, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": blk.n, "fs": blk.fs, "storage": "int16", "pop": blk.pop,
+                       "gens": blk.gens, "tier": "f64-anchored phase, f32 cos", "l2": "flushed between steps",
+                       "de_seconds": total_ms / args.steps * 1e-3, "wall_s": wall},
+            "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(blk.samples.nbytes),
+                    "d2h_bytes_per_step": 6 * 8 + 8}}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(blk) if world == 1 else None
+    if rank == 0:
+        line["fit"] = {"params": [float(v) for v in params], "sse": float(sse), "truth": [float(v) for v in blk.truth]}
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,156 @@
+/*
+ * phasetrack -- C ABI of the B300 (sm_103a) implementation of the
+ * Differential-Evolution phase-tracking hot path of arxiv 1906.10598
+ * ("The GPU-based Phase Tracking method for Planetary Radio Science
+ * applications").
+ *
+ * The paper fits each open-loop tracking block with the Taylor-phase model
+ * of Sec. 2.2 Eq. 2-2-2 (amplitude slope c5 = 0), written here in cycles:
+ *
+ *   m(t) = A cos(2 pi p(t)),   p(t) = phi0/(2 pi) + f0 t + f1 t^2/2 + f2 t^3/6
+ *
+ * so that c0 = phi0, c1 = 2 pi f0, c2 = pi f1, c3 = pi f2 / 3, c4 = A
+ * (Eq. 2-2-3). A candidate is the row theta = (A, phi0, f0, f1, f2) of five
+ * doubles. Its objective is the unit-weight chi-square of Eq. 2-2-4,
+ *
+ *   SSE(theta) = sum_{i=0}^{n-1} (s_i - m(t_i))^2,   t_i = t0 + i / fs,
+ *
+ * and the fit minimises it by DE (Sec. 1.2 and Table 3-1-1: mutation factor
+ * F, crossover CR, a fixed number of iterations as the stop rule).
+ *
+ * Conventions for every entry point:
+ *   - Return value: PT_OK (0) on success, PT_PENDING (1) for a request that
+ *     is still running, a negative PT_E* code on failure. No exception or
+ *     C++ type crosses this boundary. pt_last_error() describes the last
+ *     failure of that context as a NUL-terminated string owned by the context.
+ *   - Pointers documented as "host or device" may point to pageable or
+ *     pinned host memory or to device memory of the context's GPU; the
+ *     library detects which. All such calls are synchronous: when they return,
+ *     outputs are written and inputs may be reused.
+ *   - Contexts are not thread-safe: one thread at a time per context.
+ */
+#ifndef PHASETRACK_H
+#define PHASETRACK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Entry points are exported from the shared library; everything else is hidden. */
+#if defined(__GNUC__)
+#define PT_API __attribute__((visibility("default")))
+#else
+#define PT_API
+#endif
+
+typedef struct pt_ctx pt_ctx;
+
+/* Status codes. */
+#define PT_OK 0
+#define PT_PENDING 1
+#define PT_EINVAL (-1)    /* invalid argument (NaN bounds, lo > hi, pop < 4, n < 1, fs <= 0, ...) */
+#define PT_ENOMEM (-2)    /* device or host allocation failed */
+#define PT_EAGAIN (-3)    /* admission refused: not enough device memory or slots right now */
+#define PT_ETIMEOUT (-4)  /* a bounded device-side wait expired; the kernel returned early */
+#define PT_ECUDA (-5)     /* a CUDA runtime call failed */
+#define PT_ENOTCONV (-6)  /* a result failed its validity check */
+#define PT_ENOBLOCK (-7)  /* no block loaded in this context */
+
+/* Sample storage types of pt_load_block (Table "PRSR data recording modes":
+ * 8/16-bit quantised narrow-band samples; float types for synthetic data). */
+#define PT_I8 0
+#define PT_I16 1
+#define PT_F16 2
+#define PT_F32 3
+#define PT_F64 4
+
+/* Precision tiers of the objective.
+ *   PT_TIER_F64   (default) phase exact to ~1e-6 rad: per candidate the
+ *                 sample-index polynomial is reduced mod one cycle from FP64
+ *                 into 128-bit fixed point, re-anchored per 256-sample tile
+ *                 with integer arithmetic, walked in 32-bit fixed point;
+ *                 FP32 cosine (SFU) and FP32 residuals.
+ *   PT_TIER_PLAIN all-FP64 per sample: Horner phase in seconds, FP64
+ *                 reduction mod one cycle, FP64 cospi, FP64 residuals.
+ *   PT_TIER_DF32  per-sample phase in double-float (pairs of FP32), FP32
+ *                 cosine; no FP64 in the sample loop.
+ *   PT_TIER_F32   naive FP32 Horner phase in seconds, FP32 cosine. */
+#define PT_TIER_F64 0
+#define PT_TIER_PLAIN 1
+#define PT_TIER_DF32 2
+#define PT_TIER_F32 3
+
+/* Largest DE population supported by the device kernels. */
+#define PT_POP_MAX 128
+
+/* Create a context on CUDA device `device`. The context owns device memory,
+ * a CUDA stream and the autotune cache. *out is set on success. */
+PT_API int pt_create(pt_ctx** out, int device);
+
+/* Release a context and everything it owns. NULL is allowed. */
+PT_API void pt_destroy(pt_ctx* ctx);
+
+/* Description of the last failure on `ctx` (empty string if none). */
+PT_API const char* pt_last_error(const pt_ctx* ctx);
+
+/* Use `stream` (a cudaStream_t of the context's device) for all work of this
+ * context; NULL restores the context's own stream. The caller keeps ownership. */
+PT_API int pt_set_stream(pt_ctx* ctx, void* stream);
+
+/* The cudaStream_t the context launches on. */
+PT_API void* pt_get_stream(const pt_ctx* ctx);
+
+/* Load one data block (Sec. 2.2: a contiguous block of n samples with the
+ * time origin t0 of sample 0; a block centred on 0 has t0 = -(n-1)/(2 fs)).
+ *   samples  host or device pointer to n values of type `dtype`; copied, so
+ *            the caller keeps ownership.
+ *   n        number of samples, n >= 1.
+ *   dtype    PT_I8, PT_I16, PT_F16, PT_F32 or PT_F64.
+ *   scale    physical value of sample i is scale * samples[i] (scale > 0).
+ *   fs       sampling rate in Hz (> 0); t_i = t0 + i / fs.
+ * Replaces the context's current block. Errors: PT_EINVAL, PT_ENOMEM, PT_ECUDA. */
+PT_API int pt_load_block(pt_ctx* ctx, const void* samples, int64_t n, int dtype, double scale, double fs, double t0);
+
+/* Evaluate Eq. 2-2-4 for n candidates on the loaded block.
+ *   cands    host or device pointer, n rows of 5 doubles (A, phi0, f0, f1, f2), row-major.
+ *   sse_out  host or device pointer, n doubles.
+ *   tier     PT_TIER_*.
+ * The result is deterministic: it does not depend on the launch shape.
+ * Errors: PT_EINVAL, PT_ENOBLOCK, PT_ENOMEM, PT_ECUDA, PT_ETIMEOUT. */
+PT_API int pt_objective(pt_ctx* ctx, const double* cands, int64_t n, double* sse_out, int tier);
+
+/* Fit the loaded block by DE/rand/1/bin (Sec. 1.2, Table 3-1-1) in one
+ * persistent device launch.
+ *   bounds      host pointer, 5 x 2 doubles: (lo, hi) per parameter. The phi0
+ *               range wraps when it spans a full circle (Sec. 3.1.1: [0, 2 pi]);
+ *               other out-of-range trial components move to the midpoint of
+ *               the violated bound and the parent's component.
+ *   pop         population size, 4 <= pop <= PT_POP_MAX.
+ *   gens        generations after the initial population (itermax), >= 0.
+ *   F, CR       mutation factor and crossover rate (CR >= 1 crosses every component).
+ *   seed        Philox4x32-10 key; the draws of individual i at generation g
+ *               use counters (k, i, g, block_id), k = 0, 1, 2 (block_id 0 here).
+ *   params_out  host or device pointer, 6 doubles: best (A, phi0, f0, f1, f2)
+ *               and its SSE; written only on success. Ties go to the lowest index.
+ *   tier        PT_TIER_*.
+ * Errors: PT_EINVAL, PT_ENOBLOCK, PT_ENOMEM, PT_ECUDA, PT_ETIMEOUT. */
+PT_API int pt_de_solve(pt_ctx* ctx, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
+                double* params_out, int tier);
+
+/* pt_de_solve with a Philox block id and the final population:
+ *   pop_out  optional (NULL) host or device pointer, pop x 5 doubles.
+ *   fit_out  optional (NULL) host or device pointer, pop doubles (their SSE). */
+PT_API int pt_de_solve_ex(pt_ctx* ctx, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
+                   uint32_t block_id, double* params_out, double* pop_out, double* fit_out, int tier);
+
+/* Device time in milliseconds of the last pt_objective / pt_de_solve kernel
+ * work, measured with CUDA events on the context's stream. */
+PT_API int pt_last_kernel_ms(const pt_ctx* ctx, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHASETRACK_H */

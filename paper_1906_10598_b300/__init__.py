@@ -1,0 +1,188 @@
+"""Python binding of ``libphasetrack`` (the C ABI in ``include/phasetrack.h``).
+
+Argument marshalling only: every step of the objective and the DE fit runs in
+the library's CUDA kernels. Inputs may be numpy arrays (host memory) or torch
+CUDA tensors (device memory, passed by pointer); PyTorch is used only as a
+carrier of device memory and streams.
+
+The library must be built (``python -m paper_1906_10598_b300.build``); there is
+no CPU fallback: if the library or a GPU is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphasetrack.so")
+
+PT_OK, PT_PENDING = 0, 1
+PT_EINVAL, PT_ENOMEM, PT_EAGAIN, PT_ETIMEOUT, PT_ECUDA, PT_ENOTCONV, PT_ENOBLOCK = -1, -2, -3, -4, -5, -6, -7
+PT_I8, PT_I16, PT_F16, PT_F32, PT_F64 = 0, 1, 2, 3, 4
+TIER_F64, TIER_PLAIN, TIER_DF32, TIER_F32 = 0, 1, 2, 3
+TIERS = {"f64": TIER_F64, "plain": TIER_PLAIN, "df32": TIER_DF32, "f32": TIER_F32}
+POP_MAX = 128
+
+_NP_TO_PT = {np.dtype(np.int8): PT_I8, np.dtype(np.int16): PT_I16, np.dtype(np.float16): PT_F16,
+             np.dtype(np.float32): PT_F32, np.dtype(np.float64): PT_F64}
+_STATUS = {PT_EINVAL: "EINVAL", PT_ENOMEM: "ENOMEM", PT_EAGAIN: "EAGAIN", PT_ETIMEOUT: "ETIMEOUT",
+           PT_ECUDA: "ECUDA", PT_ENOTCONV: "ENOTCONV", PT_ENOBLOCK: "ENOBLOCK"}
+
+_lib = None
+
+
+class PhaseTrackError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load_library():
+    """Load libphasetrack.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1906_10598_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, i64, c_int = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int
+    lib.pt_create.argtypes = [ctypes.POINTER(vp), c_int]
+    lib.pt_create.restype = c_int
+    lib.pt_destroy.argtypes = [vp]
+    lib.pt_destroy.restype = None
+    lib.pt_last_error.argtypes = [vp]
+    lib.pt_last_error.restype = ctypes.c_char_p
+    lib.pt_set_stream.argtypes = [vp, vp]
+    lib.pt_set_stream.restype = c_int
+    lib.pt_get_stream.argtypes = [vp]
+    lib.pt_get_stream.restype = vp
+    lib.pt_load_block.argtypes = [vp, vp, i64, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.pt_load_block.restype = c_int
+    lib.pt_objective.argtypes = [vp, vp, i64, vp, c_int]
+    lib.pt_objective.restype = c_int
+    lib.pt_de_solve.argtypes = [vp, dp, c_int, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, vp, c_int]
+    lib.pt_de_solve.restype = c_int
+    lib.pt_de_solve_ex.argtypes = [vp, dp, c_int, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                   ctypes.c_uint32, vp, vp, vp, c_int]
+    lib.pt_de_solve_ex.restype = c_int
+    lib.pt_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.pt_last_kernel_ms.restype = c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (must be contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _is_torch(a) -> bool:
+    return hasattr(a, "data_ptr") and not isinstance(a, np.ndarray)
+
+
+class Context:
+    """One ``pt_ctx``: a GPU, its stream, the loaded block and device scratch."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        rc = self._lib.pt_create(ctypes.byref(self._h), int(device))
+        if rc != PT_OK:
+            raise PhaseTrackError(rc, f"pt_create(device={device}) failed")
+        self.n = 0
+
+    def close(self):
+        if self._h:
+            self._lib.pt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, rc: int):
+        if rc != PT_OK:
+            raise PhaseTrackError(rc, (self._lib.pt_last_error(self._h) or b"").decode())
+
+    @property
+    def stream(self) -> int:
+        return int(self._lib.pt_get_stream(self._h) or 0)
+
+    def set_stream(self, stream_handle: Optional[int]):
+        self._check(self._lib.pt_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)))
+
+    def load_block(self, samples, fs: float, t0: float, scale: float = 1.0, dtype: Optional[int] = None):
+        """pt_load_block: samples as numpy (host) or torch CUDA tensor (device)."""
+        if dtype is None:
+            if isinstance(samples, np.ndarray):
+                dtype = _NP_TO_PT[samples.dtype]
+            else:
+                import torch
+                dtype = {torch.int8: PT_I8, torch.int16: PT_I16, torch.float16: PT_F16, torch.float32: PT_F32,
+                         torch.float64: PT_F64}[samples.dtype]
+        n = int(samples.numel() if _is_torch(samples) else samples.size)
+        self._check(self._lib.pt_load_block(self._h, ctypes.c_void_p(_ptr(samples)), n, int(dtype), float(scale),
+                                            float(fs), float(t0)))
+        self.n = n
+
+    def objective(self, cands, tier: int = TIER_F64, out=None):
+        """pt_objective: SSE of each row of ``cands`` (n x 5). Returns ``out``
+        (numpy float64 if cands is numpy, else a torch tensor on the same device)."""
+        if isinstance(cands, np.ndarray):
+            c = np.ascontiguousarray(cands, dtype=np.float64).reshape(-1, 5)
+            n = c.shape[0]
+            if out is None:
+                out = np.zeros(n, dtype=np.float64)
+        else:
+            c = cands.contiguous().reshape(-1, 5)
+            n = c.shape[0]
+            if out is None:
+                import torch
+                out = torch.empty(n, dtype=torch.float64, device=c.device)
+        self._check(self._lib.pt_objective(self._h, ctypes.c_void_p(_ptr(c)), n, ctypes.c_void_p(_ptr(out)),
+                                           int(tier)))
+        return out
+
+    def de_solve(self, bounds, pop: int, gens: int, F: float, CR: float, seed: int, tier: int = TIER_F64,
+                 block_id: int = 0, return_population: bool = False):
+        """pt_de_solve_ex: returns (params[5], sse) or (params, sse, population, fitness)."""
+        b = np.ascontiguousarray(np.asarray(bounds, dtype=np.float64).reshape(5, 2))
+        out = np.zeros(6, dtype=np.float64)
+        popv = np.zeros((pop, 5), dtype=np.float64) if return_population else None
+        fit = np.zeros(pop, dtype=np.float64) if return_population else None
+        self._check(self._lib.pt_de_solve_ex(
+            self._h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(pop), int(gens), float(F), float(CR),
+            ctypes.c_uint64(int(seed)), ctypes.c_uint32(int(block_id)), ctypes.c_void_p(out.ctypes.data),
+            ctypes.c_void_p(popv.ctypes.data if popv is not None else 0),
+            ctypes.c_void_p(fit.ctypes.data if fit is not None else 0), int(tier)))
+        if return_population:
+            return out[:5].copy(), float(out[5]), popv, fit
+        return out[:5].copy(), float(out[5])
+
+    def last_kernel_ms(self) -> float:
+        v = ctypes.c_float()
+        self._check(self._lib.pt_last_kernel_ms(self._h, ctypes.byref(v)))
+        return float(v.value)

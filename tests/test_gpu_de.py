@@ -1,0 +1,129 @@
+"""GPU parity of the persistent DE solve (Sec. 1.2, Table 3-1-1) against the oracle.
+
+* The initial population (Philox draws + FP64 arithmetic) is bit-identical.
+* Early generations are bit-identical: selection only flips on SSE near-ties.
+* Fits: phi0 within 1e-3 rad (mod 2 pi) and f0 within 1e-5 Hz of the oracle's
+  fit on blocks where the oracle reached the global basin.
+* Full-size 400K block in the benchmark's launch configuration: sampled checks
+  the oracle can afford (SSE at the fitted and true parameters).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    build.build()
+    c = pt.Context(0)
+    yield c
+    c.close()
+
+
+def _wrap(d):
+    return np.angle(np.exp(1j * d))
+
+
+@pytest.mark.parametrize("pop,seed,block_id", [(4, 0, 0), (5, 1, 3), (17, 2 ** 40 + 7, 0), (64, 123, 9),
+                                               (128, 0xFFFFFFFFFFFF, 1)])
+def test_initial_population_bit_identical(ctx, pop, seed, block_id):
+    import paper_1906_10598_b300 as pt
+    blk = synth.single4096(1, n=1000)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    _, _, gpop, _ = ctx.de_solve(blk.bounds, pop, 0, 0.7, 0.9, seed, pt.TIER_PLAIN, block_id=block_id,
+                                 return_population=True)
+    _, _, opop, _ = oracle.de_solve(blk.values(), blk.fs, blk.t0, blk.bounds, pop, 0, 0.7, 0.9, seed,
+                                    block_id=block_id, return_population=True)
+    assert np.array_equal(gpop, opop)
+
+
+@pytest.mark.parametrize("tier_name", ["plain", "f64"])
+def test_early_generations_bit_identical(ctx, tier_name):
+    import paper_1906_10598_b300 as pt
+    blk = synth.single4096(3)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    for gens, CR in ((1, 0.9), (6, 0.9), (6, 1.0)):
+        _, _, gpop, gfit = ctx.de_solve(blk.bounds, 32, gens, 0.7, CR, 77, pt.TIERS[tier_name],
+                                        return_population=True)
+        _, _, opop, ofit = oracle.de_solve(blk.values(), blk.fs, blk.t0, blk.bounds, 32, gens, 0.7, CR, 77,
+                                           return_population=True)
+        same = np.all(gpop == opop, axis=1)
+        # a member can differ only if a selection compared two SSEs closer than the tier's error
+        assert same.sum() >= 31, (gens, CR, np.where(~same))
+        tol = 1e-9 if tier_name == "plain" else 1e-6
+        assert np.all(np.abs(gfit[same] - ofit[same]) <= tol * ofit[same])
+
+
+def test_single4096_plain_fit_matches_oracle(ctx):
+    # the N = 4096 FP64 block, pop 32, 200 generations, F 0.7, CR 0.9, seed 0, FP64 plain method
+    import paper_1906_10598_b300 as pt
+    checked = 0
+    for seed in range(4):
+        blk = synth.single4096(seed)
+        ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+        g, gf = ctx.de_solve(blk.bounds, blk.pop, blk.gens, blk.F, blk.CR, blk.de_seed, pt.TIER_PLAIN)
+        o, of = oracle.de_solve(blk.values(), blk.fs, blk.t0, blk.bounds, blk.pop, blk.gens, blk.F, blk.CR,
+                                blk.de_seed)
+        assert gf == pytest.approx(oracle.sse(blk.values(), blk.fs, blk.t0, g), rel=1e-9)
+        if of <= oracle.sse(blk.values(), blk.fs, blk.t0, blk.truth) + 30 * blk.sigma ** 2:
+            checked += 1
+            assert abs(_wrap(g[1] - o[1])) <= 1e-3
+            assert abs(g[2] - o[2]) <= 1e-5
+    assert checked >= 1
+
+
+def test_default_tier_fit_matches_oracle(ctx):
+    import paper_1906_10598_b300 as pt
+    blk = synth.paper400k(4, n=40_000, fs=10_000.0, gens=300)
+    blk.pop = 32
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    g, gf = ctx.de_solve(blk.bounds, blk.pop, blk.gens, blk.F, blk.CR, 5, pt.TIER_F64)
+    o, of = oracle.de_solve(blk.values(), blk.fs, blk.t0, blk.bounds, blk.pop, blk.gens, blk.F, blk.CR, 5)
+    assert gf == pytest.approx(oracle.sse(blk.values(), blk.fs, blk.t0, g), rel=1e-6)
+    assert of <= oracle.sse(blk.values(), blk.fs, blk.t0, blk.truth) * (1 + 1e-4)
+    assert abs(_wrap(g[1] - o[1])) <= 1e-3
+    assert abs(g[2] - o[2]) <= 1e-5
+
+
+def test_paper400k_full_size_sampled(ctx):
+    # N = 400,000 int16, pop 64, 1250 generations: the benchmark's configuration
+    import paper_1906_10598_b300 as pt
+    blk = synth.paper400k(0)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    g, gf = ctx.de_solve(blk.bounds, blk.pop, blk.gens, blk.F, blk.CR, blk.de_seed, pt.TIER_F64)
+    s = blk.values()
+    at_fit = oracle.sse(s, blk.fs, blk.t0, g)
+    at_truth = oracle.sse(s, blk.fs, blk.t0, blk.truth)
+    assert gf == pytest.approx(at_fit, rel=1e-6)
+    # global basin: the fit is no worse than the truth (up to the fit's own noise gain)
+    assert at_fit <= at_truth * (1 + 1e-6)
+    crb = oracle.crb(blk.truth, blk.n, blk.fs, blk.t0, blk.sigma)
+    assert abs(g[2] - blk.truth[2]) <= 6 * crb[2] + 1e-9
+    # repeated solve is bit-identical
+    g2, gf2 = ctx.de_solve(blk.bounds, blk.pop, blk.gens, blk.F, blk.CR, blk.de_seed, pt.TIER_F64)
+    assert np.array_equal(g, g2) and gf == gf2
+
+
+def test_de_invalid_arguments(ctx):
+    import paper_1906_10598_b300 as pt
+    blk = synth.single4096(0, n=500)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    b = np.array(blk.bounds)
+    for pop in (3, 129):
+        with pytest.raises(pt.PhaseTrackError) as e:
+            ctx.de_solve(b, pop, 5, 0.7, 0.9, 0)
+        assert e.value.code == pt.PT_EINVAL
+    bad = b.copy()
+    bad[2] = (bad[2, 1], bad[2, 0])  # lo > hi
+    with pytest.raises(pt.PhaseTrackError):
+        ctx.de_solve(bad, 16, 5, 0.7, 0.9, 0)
+    nanb = b.copy()
+    nanb[0, 0] = np.nan
+    with pytest.raises(pt.PhaseTrackError):
+        ctx.de_solve(nanb, 16, 5, 0.7, 0.9, 0)
