@@ -108,7 +108,7 @@ class ClockSampler:
                 "samples": len(sm), "sm_mhz_min": float(min(sm))}
 
 
-def cpu_baseline(blk: synth.Block, gens: int = 8):
+def cpu_baseline(blk: synth.Block, gens: int = 240):
     """The oracle (FP64, libm cos, OpenMP over candidates) timed on this host's
     cores on a bounded sample of the workload: the same block and population
     for `gens` generations instead of 1250."""
@@ -248,7 +248,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
