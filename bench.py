@@ -161,7 +161,10 @@ def run_gpu(args):
     build.build()
     blk = synth.paper400k(rank)
     ctx = pt.Context(local)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library launches on it and the CUDA events below
+    # are recorded on it, so they bracket exactly the library's work
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx.set_stream(stream.cuda_stream)
     ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2

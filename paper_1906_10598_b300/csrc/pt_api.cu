@@ -107,60 +107,99 @@ int kernel_error(pt_ctx* c) {
   return PT_OK;
 }
 
+// Candidates per work item for the default tier: the width in {16, 8, 4}
+// that pads `n` the least (wider on ties); the other tiers use 8.
+int pick_cg(int tier, int n) {
+  if (tier != PT_TIER_F64) return 8;
+  int best = 16, best_pad = (n + 15) / 16 * 16;
+  for (int cg : {8, 4}) {
+    const int pad = (n + cg - 1) / cg * cg;
+    if (pad < best_pad) {
+      best = cg;
+      best_pad = pad;
+    }
+  }
+  return best;
+}
+
 // ---- objective -------------------------------------------------------------
 
-template <int TIER>
+template <int TIER, int CGV>
 int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
   const BlockArgs& b = c->blk;
   ObjArgs a{};
   a.b = b;
   a.cands = d_cands;
   a.ncand = ncand;
-  a.cpc = std::min(((ncand + CG - 1) / CG) * CG, NP_MAX);
+  a.cpc = std::min(((ncand + CGV - 1) / CGV) * CGV, NP_MAX);
   const int ny = (ncand + a.cpc - 1) / a.cpc;
   // about two CTAs per SM in total, tiles split evenly
   const int64_t want = 2LL * c->sms;
   int64_t tpc = (b.ntiles * ny + want - 1) / want;
   tpc = std::max<int64_t>(1, std::min<int64_t>(tpc, 32));
   a.tpc = (int)tpc;
-  a.tiles_chunk = std::min(a.tpc, 8);
   const int nx = (int)((b.ntiles + a.tpc - 1) / a.tpc);
   a.acc = c->d_acc;
   a.err = c->d_err;
   a.timeout_ns = c->timeout_ns;
-  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, a.tiles_chunk, b.esize, 0);
+  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, b.esize, 0, NT);
   if (S.total > c->smem_optin) return fail(c, PT_EINVAL, "objective launch needs too much shared memory");
-  PT_CUDA(c, cudaFuncSetAttribute(k_objective<TIER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
+  PT_CUDA(c, cudaFuncSetAttribute(k_objective<TIER, CGV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)S.total));
   dim3 grid(nx, ny);
-  k_objective<TIER><<<grid, NT, S.total, c->stream>>>(a);
+  k_objective<TIER, CGV><<<grid, NT, S.total, c->stream>>>(a);
   PT_CUDA(c, cudaGetLastError());
   return PT_OK;
 }
 
+int launch_objective_any(pt_ctx* c, int tier, const double* d_cands, int ncand) {
+  switch (tier) {
+    case PT_TIER_F64: {
+      const int cg = pick_cg(tier, std::min(ncand, NP_MAX));
+      if (cg == 16) return launch_objective<TIER_F64, 16>(c, d_cands, ncand);
+      if (cg == 8) return launch_objective<TIER_F64, 8>(c, d_cands, ncand);
+      return launch_objective<TIER_F64, 4>(c, d_cands, ncand);
+    }
+    case PT_TIER_PLAIN: return launch_objective<TIER_PLAIN, 8>(c, d_cands, ncand);
+    case PT_TIER_DF32: return launch_objective<TIER_DF32, 8>(c, d_cands, ncand);
+    default: return launch_objective<TIER_F32, 8>(c, d_cands, ncand);
+  }
+}
+
 // ---- DE --------------------------------------------------------------------
 
-template <int TIER>
+template <int TIER, int CGV>
 int launch_de(pt_ctx* c, DeArgs& a) {
   const BlockArgs& b = c->blk;
+  a.npad = (a.np + CGV - 1) / CGV * CGV;
   a.nctas = (int)std::min<int64_t>(b.ntiles, c->sms);
   a.tmax = (int)((b.ntiles + a.nctas - 1) / a.nctas);
-  a.tiles_chunk = std::min(a.tmax, 16);
-  SmemLayout S = smem_layout(TIER, a.npad, a.tmax, a.tiles_chunk, b.esize, a.npad);
-  while (S.total > c->smem_optin && a.tiles_chunk > 1) {
-    a.tiles_chunk /= 2;
-    S = smem_layout(TIER, a.npad, a.tmax, a.tiles_chunk, b.esize, a.npad);
-  }
+  const SmemLayout S = smem_layout(TIER, a.npad, a.tmax, CGV, b.esize, a.npad, NT);
   if (S.total > c->smem_optin)
     return fail(c, PT_EINVAL, "block too long for the resident DE kernel (" + std::to_string(S.total) +
                                   " bytes of shared memory per CTA)");
-  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
+  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, CGV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
   int occ = 0;
-  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER>, NT, S.total));
+  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, CGV>, NT, S.total));
   if (occ < 1 || a.nctas > occ * c->sms) return fail(c, PT_EINVAL, "DE grid cannot be co-resident");
   void* args[] = {&a};
-  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER>, dim3(a.nctas), dim3(NT), args, S.total,
+  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, CGV>, dim3(a.nctas), dim3(NT), args, S.total,
                                          c->stream));
   return PT_OK;
+}
+
+int launch_de_any(pt_ctx* c, int tier, DeArgs& a) {
+  switch (tier) {
+    case PT_TIER_F64: {
+      const int cg = pick_cg(tier, a.np);
+      if (cg == 16) return launch_de<TIER_F64, 16>(c, a);
+      if (cg == 8) return launch_de<TIER_F64, 8>(c, a);
+      return launch_de<TIER_F64, 4>(c, a);
+    }
+    case PT_TIER_PLAIN: return launch_de<TIER_PLAIN, 8>(c, a);
+    case PT_TIER_DF32: return launch_de<TIER_DF32, 8>(c, a);
+    default: return launch_de<TIER_F32, 8>(c, a);
+  }
 }
 
 }  // namespace
@@ -274,6 +313,7 @@ int pt_load_block(pt_ctx* c, const void* samples, int64_t n, int dtype, double s
   b.esize = es;
   b.scale = scale;
   b.smax = amax * scale;
+  b.smax_f = (float)b.smax;
   if (!std::isfinite(b.smax)) return fail(c, PT_EINVAL, "pt_load_block: non-finite samples");
   b.t0 = t0;
   b.h = 1.0 / fs;
@@ -306,14 +346,9 @@ int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int
   PT_CUDA(c, cudaMemsetAsync(c->d_acc, 0, (size_t)n * sizeof(unsigned long long), c->stream));
   PT_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   PT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-  switch (tier) {
-    case PT_TIER_F64: rc = launch_objective<TIER_F64>(c, d_c, (int)n); break;
-    case PT_TIER_PLAIN: rc = launch_objective<TIER_PLAIN>(c, d_c, (int)n); break;
-    case PT_TIER_DF32: rc = launch_objective<TIER_DF32>(c, d_c, (int)n); break;
-    default: rc = launch_objective<TIER_F32>(c, d_c, (int)n); break;
-  }
+  rc = launch_objective_any(c, tier, d_c, (int)n);
   if (rc != PT_OK) return rc;
-  k_finalize<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(d_c, (int)n, c->d_acc, c->blk.n, c->blk.smax, d_out);
+  k_finalize<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(d_c, (int)n, c->d_acc, c->blk.n, c->blk.smax_f, d_out);
   PT_CUDA(c, cudaGetLastError());
   PT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   if (!dev_out)
@@ -350,26 +385,17 @@ int pt_de_solve_ex(pt_ctx* c, const double* bounds, int pop, int gens, double F,
   a.dc.key = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
   a.dc.block_id = block_id;
   a.np = pop;
-  a.npad = (pop + CG - 1) / CG * CG;
   a.gens = gens;
   a.gacc = c->d_gacc;
-  a.bar = c->d_bar;
   a.err = c->d_err;
   a.out = c->d_out;
   a.pop_out = c->d_pop;
   a.fit_out = c->d_fit;
   a.timeout_ns = c->timeout_ns;
   PT_CUDA(c, cudaMemsetAsync(c->d_gacc, 0, 3 * PT_POP_MAX * sizeof(unsigned long long), c->stream));
-  PT_CUDA(c, cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned), c->stream));
   PT_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   PT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-  int rc;
-  switch (tier) {
-    case PT_TIER_F64: rc = launch_de<TIER_F64>(c, a); break;
-    case PT_TIER_PLAIN: rc = launch_de<TIER_PLAIN>(c, a); break;
-    case PT_TIER_DF32: rc = launch_de<TIER_DF32>(c, a); break;
-    default: rc = launch_de<TIER_F32>(c, a); break;
-  }
+  int rc = launch_de_any(c, tier, a);
   if (rc != PT_OK) return rc;
   PT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   if ((rc = kernel_error(c)) != PT_OK) return rc;

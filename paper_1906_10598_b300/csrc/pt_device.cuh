@@ -26,7 +26,6 @@ typedef unsigned __int128 u128;
 constexpr int D = 5;             // (A, phi0, f0, f1, f2)
 constexpr int M = 8;             // samples per lane per tile
 constexpr int L = 32 * M;        // samples per tile
-constexpr int CG = 8;            // candidates per work item
 constexpr int NP_MAX = 128;      // largest population / candidate batch per CTA
 
 constexpr double TWO_PI = 2.0 * 3.14159265358979323846;
@@ -48,6 +47,7 @@ struct BlockArgs {
   int esize;             // bytes per stored sample
   double scale;          // physical = scale * stored
   double smax;           // max |physical sample|
+  float smax_f;          // smax rounded to FP32 (sets the SSE fixed-point scale)
   double t0, h;          // t_i = t0 + i h
   double t0sq_2, t0cu_6; // t0^2/2, t0^3/6
   double h2_2, h3_6;     // h^2/2, h^3/6
@@ -62,6 +62,12 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -129,11 +135,18 @@ __device__ __forceinline__ void de_init(const DeControls& dc, int i, double* xi)
     xi[j] = __dadd_rn(dc.lo[j], __dmul_rn(u53(w[2 * j], w[2 * j + 1]), __dsub_rn(dc.hi[j], dc.lo[j])));
 }
 
-// DE/rand/1/bin trial of individual i at generation gen >= 1 from population x (np x 5).
-// FP64 operations are written out with _rn intrinsics so no contraction
-// changes a rounding: the trial is bit-identical to a plain IEEE evaluation.
-__device__ __forceinline__ void de_trial(const DeControls& dc, const double* x, int np, int i, uint32_t gen,
-                                         double* ui) {
+// Order-preserving integer key of a finite double: a < b  <=>  key(a) < key(b).
+// Comparisons in the DE run on the integer pipes (B300's FP64 pipe is 1/64 rate).
+__device__ __forceinline__ long long dkey(double a) {
+  const long long b = __double_as_longlong(a);
+  return b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b);
+}
+
+// Random draws of individual i at generation gen >= 1 (selection-independent):
+// r1, r2, r3 packed in bytes 0..2 (distinct, != i), crossover mask in `take`
+// (bit j set = component j comes from the mutant).
+__device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, uint32_t gen, uint32_t* rpack,
+                                         uint32_t* take) {
   uint32_t w[12];
   de_draw12(dc.key, dc.block_id, gen, (uint32_t)i, w);
   // three distinct indices != i, by index shifting over the sorted exclusions
@@ -155,25 +168,36 @@ __device__ __forceinline__ void de_trial(const DeControls& dc, const double* x, 
     nex++;
   }
   const uint32_t jrand = lemire(w[3], (uint32_t)D);
+  uint32_t m = 0;
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    const double parent = x[i * D + j];
-    const bool take = (uint32_t)j == jrand || dc.cr_all || w[4 + j] < dc.cr_thr;
-    double u = parent;
-    if (take) {
-      double v = __dadd_rn(x[r[0] * D + j], __dmul_rn(dc.F, __dsub_rn(x[r[1] * D + j], x[r[2] * D + j])));
-      if (j == 1 && dc.periodic) {
-        const double k = floor(__ddiv_rn(__dsub_rn(v, dc.lo[j]), TWO_PI));
-        v = __dsub_rn(v, __dmul_rn(k, TWO_PI));
-      } else if (v < dc.lo[j]) {
-        v = __dmul_rn(__dadd_rn(dc.lo[j], parent), 0.5);
-      } else if (v > dc.hi[j]) {
-        v = __dmul_rn(__dadd_rn(dc.hi[j], parent), 0.5);
-      }
-      u = v;
+  for (int j = 0; j < D; ++j)
+    if ((uint32_t)j == jrand || dc.cr_all || w[4 + j] < dc.cr_thr) m |= 1u << j;
+  *rpack = r[0] | (r[1] << 8) | (r[2] << 16);
+  *take = m;
+}
+
+// Component j of the DE/rand/1/bin trial of individual i from population x
+// (np x 5). FP64 operations use _rn intrinsics so no contraction changes a
+// rounding: the value is bit-identical to a plain IEEE evaluation.
+__device__ __forceinline__ double de_component(const DeControls& dc, const double* x, int i, int j, uint32_t rpack,
+                                               uint32_t take) {
+  const double parent = x[i * D + j];
+  if (!((take >> j) & 1u)) return parent;
+  const int r0 = rpack & 0xff, r1 = (rpack >> 8) & 0xff, r2 = (rpack >> 16) & 0xff;
+  double v = __dadd_rn(x[r0 * D + j], __dmul_rn(dc.F, __dsub_rn(x[r1 * D + j], x[r2 * D + j])));
+  if (j == 1 && dc.periodic) {
+    const double d = __dsub_rn(v, dc.lo[j]);
+    // floor(d / 2pi) is 0 without dividing when 0 <= d is safely below 2pi
+    if (dkey(d) < 0 || dkey(d) >= dkey(TWO_PI * (1.0 - 0x1p-50))) {
+      const double k = floor(__ddiv_rn(d, TWO_PI));
+      v = __dsub_rn(v, __dmul_rn(k, TWO_PI));
     }
-    ui[j] = u;
+  } else if (dkey(v) < dkey(dc.lo[j])) {
+    v = __dmul_rn(__dadd_rn(dc.lo[j], parent), 0.5);
+  } else if (dkey(v) > dkey(dc.hi[j])) {
+    v = __dmul_rn(__dadd_rn(dc.hi[j], parent), 0.5);
   }
+  return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -200,78 +224,108 @@ struct Poly {
   u128 e[4];  // E0..E3 as fractions of a cycle
 };
 
-// E0..E3 of candidate th = (A, phi0, f0, f1, f2) for the block's time base.
-__device__ __forceinline__ Poly make_poly(const double* th, const BlockArgs& b) {
+// Coefficient E_k (k = 0..3) of candidate th = (A, phi0, f0, f1, f2) for the
+// block's time base, reduced mod 1 into a 128-bit fraction:
+//   E3 = f2 h^3/6,  E2 = (f1 + f2 t0) h^2/2,  E1 = (f0 + f1 t0 + f2 t0^2/2) h,
+//   E0 = phi0/(2 pi) + f0 t0 + f1 t0^2/2 + f2 t0^3/6.
+__device__ __forceinline__ u128 poly_term(const double* th, const BlockArgs& b, int k) {
   const double phi0 = th[1], f0 = th[2], f1 = th[3], f2 = th[4];
-  Poly P;
-  const double E3 = f2 * b.h3_6;
-  const double E2 = fma(f2, b.t0, f1) * b.h2_2;
-  const double E1 = fma(f2, b.t0sq_2, fma(f1, b.t0, f0)) * b.h;
-  // E0 = phi0/(2 pi) + f0 t0 + f1 t0^2/2 + f2 t0^3/6
-  const double E0 = fma(f2, b.t0cu_6, fma(f1, b.t0sq_2, fma(f0, b.t0, phi0 * INV_TWO_PI)));
-  P.e[0] = frac128(E0);
-  P.e[1] = frac128(E1);
-  P.e[2] = frac128(E2);
-  P.e[3] = frac128(E3);
-  return P;
+  double E;
+  if (k == 3) E = f2 * b.h3_6;
+  else if (k == 2) E = fma(f2, b.t0, f1) * b.h2_2;
+  else if (k == 1) E = fma(f2, b.t0sq_2, fma(f1, b.t0, f0)) * b.h;
+  else E = fma(f2, b.t0cu_6, fma(f1, b.t0sq_2, fma(f0, b.t0, phi0 * INV_TWO_PI)));
+  return frac128(E);
+}
+
+// x * y mod 2^128 for a 64-bit y.
+__device__ __forceinline__ u128 mul_u128_u64(u128 x, uint64_t y) {
+  const uint64_t xl = (uint64_t)x, xh = (uint64_t)(x >> 64);
+  const uint64_t lo = xl * y, hi = __umul64hi(xl, y) + xh * y;
+  return ((u128)hi << 64) | lo;
+}
+
+// A signed 64-bit integer as FP32 (two 32-bit conversions, relative error
+// below 2^-23), avoiding the slow 64-bit conversion path.
+__device__ __forceinline__ float i64_to_f32(long long v) {
+  const bool neg = v < 0;
+  const unsigned long long a = neg ? (0ull - (unsigned long long)v) : (unsigned long long)v;
+  const float f = fmaf((float)(uint32_t)(a >> 32), 4294967296.0f, (float)(uint32_t)a);
+  return neg ? -f : f;
 }
 
 // Tile anchor for samples i0 + k, k in [0, L): (U0, V, 2 pi D2, 2 pi D3) with
-// U0, V the 32-bit rounded P and D1 and the FP32 small-term coefficients.
+// U0, V the 32-bit rounded P and D1 and the FP32 small-term coefficients, from
+//   P  = E0 + i0 (E1 + i0 (E2 + i0 E3)),  D1 = E1 + i0 (2 E2 + 3 i0 E3),
+//   D2 = E2 + 3 i0 E3  (exact mod 2^128).
 __device__ __forceinline__ uint4 make_anchor(const Poly& P, uint64_t i0) {
-  const u128 I = i0, I2 = I * I, I3 = I2 * I;
-  const u128 Pp = P.e[0] + P.e[1] * I + P.e[2] * I2 + P.e[3] * I3;
-  const u128 D1 = P.e[1] + ((P.e[2] * I) << 1) + (u128)3 * P.e[3] * I2;
-  const u128 D2 = P.e[2] + (u128)3 * P.e[3] * I;
+  const u128 e3i = mul_u128_u64(P.e[3], i0);
+  const u128 Pp = P.e[0] + mul_u128_u64(P.e[1] + mul_u128_u64(P.e[2] + e3i, i0), i0);
+  const u128 e3i3 = e3i + (e3i << 1);
+  const u128 D1 = P.e[1] + mul_u128_u64((P.e[2] << 1) + e3i3, i0);
+  const u128 D2 = P.e[2] + e3i3;
   const u128 half = ((u128)1) << 95;
   const uint32_t U0 = (uint32_t)((Pp + half) >> 96);
   const uint32_t V = (uint32_t)((D1 + half) >> 96);
-  const float e2 = (float)(long long)(uint64_t)(D2 >> 64) * TWO_PI_2M64;
-  const float e3 = (float)(long long)(uint64_t)(P.e[3] >> 64) * TWO_PI_2M64;
+  const float e2 = i64_to_f32((long long)(uint64_t)(D2 >> 64)) * TWO_PI_2M64;
+  const float e3 = i64_to_f32((long long)(uint64_t)(P.e[3] >> 64)) * TWO_PI_2M64;
   return make_uint4(U0, V, __float_as_uint(e2), __float_as_uint(e3));
 }
 
 // Exponent k of the fixed-point SSE accumulator of a candidate: every
-// partial and the total are below n (smax + |A|)^2 < 2^(61-k) * 2^k ... i.e.
-// scaled values stay below 2^61.
-__device__ __forceinline__ int sse_scale_exp(int64_t n, double smax, double A) {
-  const double a = smax + fabs(A);
-  double B = (double)n * a * a;
-  if (!(B > 1e-200)) B = 1e-200;
-  int e;
-  frexp(B, &e);  // B < 2^e
-  int k = 61 - e;
+// partial and the total are at most B = n (smax + |A|)^2, and k is chosen so
+// that B * 2^k < 2^(bits+1). Computed in FP32 with a factor-2 margin for
+// rounding (B_f in [2^(e-1), 2^e) gives B < 2^(e+1), k = bits - e).
+// The objective uses bits = 60; the DE uses 53 and keeps 8 low bits of each
+// 64-bit accumulator for the arrival count.
+constexpr int SSE_BITS_OBJ = 60;
+constexpr int SSE_BITS_DE = 53;
+__device__ __forceinline__ int sse_scale_exp(int64_t n, float smax, float absA, int bits) {
+  const float a = smax + absA;
+  float B = (float)n * a * a;
+  if (!(B > 1e-30f)) B = 1e-30f;
+  const int e = (int)((__float_as_uint(B) >> 23) & 0xff) - 126;  // B in [2^(e-1), 2^e)
+  int k = bits - e;
   if (k > 120) k = 120;
   if (k < -120) k = -120;
   return k;
 }
 
+// acc * 2^-k as a double, exactly as ldexp would (acc < 2^61, |k| <= 120).
+__device__ __forceinline__ double fixed_to_double(unsigned long long acc, int k) {
+  if (acc == 0ull) return 0.0;
+  const double v = (double)(long long)acc;
+  return __longlong_as_double(__double_as_longlong(v) - ((long long)k << 52));
+}
+
 __device__ __forceinline__ float exp2_int_f(int k) { return __int_as_float((k + 127) << 23); }
 
 // ---------------------------------------------------------------------------
-// Warp reduce-scatter of 8 per-lane values: returns the full-warp sum of value
-// index (lane >> 2) & 7 (lanes 4c..4c+3 hold the sum of value c).
-template <typename T>
-__device__ __forceinline__ T warp_reduce_scatter8(const T (&v)[8], int lane) {
-  const unsigned FULL = 0xffffffffu;
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-  T w[4];
+// Warp reduce-scatter of N per-lane values (N a power of two <= 32): returns
+// the full-warp sum of value index lane / (32 / N); the 32 / N consecutive
+// lanes that share an index all hold that sum. log2(N) halving exchanges
+// (N - 1 shuffles) followed by an all-reduce over the remaining lane bits.
+template <int N, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(const T (&v)[N], int lane) {
+  T cur[N];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const T keep = b4 ? v[4 + j] : v[j];
-    const T send = b4 ? v[j] : v[4 + j];
-    w[j] = keep + __shfl_xor_sync(FULL, send, 16);
-  }
-  T y[2];
+  for (int j = 0; j < N; ++j) cur[j] = v[j];
+  int off = 16;
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const T keep = b3 ? w[2 + j] : w[j];
-    const T send = b3 ? w[j] : w[2 + j];
-    y[j] = keep + __shfl_xor_sync(FULL, send, 8);
+  for (int n = N; n > 1; n >>= 1) {
+    const bool bit = lane & off;
+#pragma unroll
+    for (int j = 0; j < n / 2; ++j) {
+      const T keep = bit ? cur[n / 2 + j] : cur[j];
+      const T send = bit ? cur[j] : cur[n / 2 + j];
+      cur[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+    off >>= 1;
   }
-  T z = (b2 ? y[1] : y[0]) + __shfl_xor_sync(FULL, b2 ? y[0] : y[1], 4);
-  z += __shfl_xor_sync(FULL, z, 2);
-  z += __shfl_xor_sync(FULL, z, 1);
+  T z = cur[0];
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1)
+    if (o <= off) z += __shfl_xor_sync(0xffffffffu, z, o);
   return z;
 }
 

@@ -7,7 +7,7 @@
 // Work decomposition shared by the objective and DE kernels: a CTA owns a
 // contiguous range of 256-sample tiles, staged once into shared memory by a
 // bulk (TMA) copy and converted to the compute type; a work item is one tile
-// x 8 candidates, run by one warp with 8 consecutive samples per lane in
+// x CG candidates (CG = 4, 8 or 16), run by one warp with 8 consecutive samples per lane in
 // registers. Per-item FP32 sums are reduced across the warp and added, as
 // 64-bit fixed point with a per-candidate scale, to shared and then global
 // accumulators. Integer addition is exact and associative, so the SSE does not
@@ -63,14 +63,14 @@ __device__ __forceinline__ dfloat df_from_double(double v) {
 //   TIER_F32:   float[4]  = c0..c3
 template <int TIER>
 __device__ __forceinline__ void prep_candidate(const double* th, const BlockArgs& b, unsigned char* cdata,
-                                               float* negA, int* kexp) {
-  *negA = -__double2float_rn(th[0]);
-  *kexp = sse_scale_exp(b.n, b.smax, th[0]);
+                                               float* negA, int* kexp, int kbits) {
+  const float Af = __double2float_rn(th[0]);
+  *negA = -Af;
+  *kexp = sse_scale_exp(b.n, b.smax_f, fabsf(Af), kbits);
   if (TIER == TIER_F64) {
-    Poly P = make_poly(th, b);
     u128* e = reinterpret_cast<u128*>(cdata);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) e[k] = P.e[k];
+    for (int k = 0; k < 4; ++k) e[k] = poly_term(th, b, k);
   } else if (TIER == TIER_PLAIN) {
     double* c = reinterpret_cast<double*>(cdata);
     c[0] = th[0];
@@ -101,18 +101,47 @@ __device__ __forceinline__ void prep_zero(unsigned char* cdata, float* negA, int
   for (int k = 0; k < CAND_BYTES / 16; ++k) p[k] = make_uint4(0, 0, 0, 0);
 }
 
+// Prepare candidates [0, nc) of `cands` (rows of 5 doubles) padded to npad.
+// The default tier spreads the four FP64 polynomial terms and the amplitude
+// over separate threads so the 1/64-rate FP64 work is spread across all
+// warps of the CTA. Ends with __syncthreads().
+template <int TIER>
+__device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs& b, unsigned char* cdata,
+                         float* negA, int* kexp, int kbits) {
+  if (TIER == TIER_F64) {
+    for (int t = threadIdx.x; t < 5 * npad; t += blockDim.x) {
+      const int k = t / npad, c = t - k * npad;
+      if (k < 4) {
+        reinterpret_cast<u128*>(cdata + c * CAND_BYTES)[k] = c < nc ? poly_term(cands + c * D, b, k) : (u128)0;
+      } else if (c < nc) {
+        const float Af = __double2float_rn(cands[c * D]);
+        negA[c] = -Af;
+        kexp[c] = sse_scale_exp(b.n, b.smax_f, fabsf(Af), kbits);
+      } else {
+        negA[c] = 0.f;
+        kexp[c] = 0;
+      }
+    }
+  } else {
+    for (int c = threadIdx.x; c < npad; c += blockDim.x) {
+      if (c < nc) prep_candidate<TIER>(cands + c * D, b, cdata + c * CAND_BYTES, negA + c, kexp + c, kbits);
+      else prep_zero(cdata + c * CAND_BYTES, negA + c, kexp + c);
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
-// Work items.
+// Work items: one warp, one 256-sample tile, CGV candidates, 8 samples per lane.
 
 // Default tier: 32-bit fixed-point phase walk + FP32 small terms + SFU cosine.
-template <bool MASKED>
-__device__ __forceinline__ void item_f64(const float (&s)[M], const uint4* anc_t, const float* negA, int g, int lane,
-                                         int nvalid, const float (&kk)[M], const float (&kkk)[M], float (&acc)[CG]) {
+template <int CGV, bool MASKED>
+__device__ __forceinline__ void item_f64(const float (&s)[M], const uint4* anc_i, const float* negA_g, int lane,
+                                         int nvalid, const float (&kk)[M], const float (&kkk)[M], float (&acc)[CGV]) {
 #pragma unroll
-  for (int c = 0; c < CG; ++c) {
-    const int cand = g * CG + c;
-    const uint4 a = anc_t[cand];
-    const float nA = negA[cand];
+  for (int c = 0; c < CGV; ++c) {
+    const uint4 a = anc_i[c];
+    const float nA = negA_g[c];
     const uint32_t V = a.y;
     uint32_t u = a.x + (uint32_t)(lane * M) * V;
     const float E2 = __uint_as_float(a.z), E3 = __uint_as_float(a.w);
@@ -132,12 +161,12 @@ __device__ __forceinline__ void item_f64(const float (&s)[M], const uint4* anc_t
 }
 
 // All-FP64 tier: Horner phase in seconds, reduction mod 1, FP64 cospi.
-template <bool MASKED>
-__device__ __forceinline__ void item_plain(const double (&s)[M], const unsigned char* cdata, int g, int lane,
-                                           int nvalid, int64_t tstart, const BlockArgs& b, double (&acc)[CG]) {
+template <int CGV, bool MASKED>
+__device__ __forceinline__ void item_plain(const double (&s)[M], const unsigned char* cdata_g, int lane, int nvalid,
+                                           int64_t tstart, const BlockArgs& b, double (&acc)[CGV]) {
 #pragma unroll 1
-  for (int c = 0; c < CG; ++c) {
-    const double* k = reinterpret_cast<const double*>(cdata + (g * CG + c) * CAND_BYTES);
+  for (int c = 0; c < CGV; ++c) {
+    const double* k = reinterpret_cast<const double*>(cdata_g + c * CAND_BYTES);
     const double A = k[0], c0 = k[1], c1 = k[2], c2 = k[3], c3 = k[4];
     double sum = 0.0;
 #pragma unroll
@@ -156,15 +185,15 @@ __device__ __forceinline__ void item_plain(const double (&s)[M], const unsigned 
 }
 
 // Double-float tier: per-sample phase in double-float, FP32 cosine.
-template <bool MASKED>
-__device__ __forceinline__ void item_df32(const float (&s)[M], const unsigned char* cdata, const float* negA, int g,
+template <int CGV, bool MASKED>
+__device__ __forceinline__ void item_df32(const float (&s)[M], const unsigned char* cdata_g, const float* negA_g,
                                           int lane, int nvalid, int64_t tstart, dfloat t0d, dfloat hd,
-                                          float (&acc)[CG]) {
+                                          float (&acc)[CGV]) {
 #pragma unroll 1
-  for (int c = 0; c < CG; ++c) {
-    const dfloat* k = reinterpret_cast<const dfloat*>(cdata + (g * CG + c) * CAND_BYTES);
+  for (int c = 0; c < CGV; ++c) {
+    const dfloat* k = reinterpret_cast<const dfloat*>(cdata_g + c * CAND_BYTES);
     const dfloat c0 = k[0], c1 = k[1], c2 = k[2], c3 = k[3];
-    const float nA = negA[g * CG + c];
+    const float nA = negA_g[c];
     float sum = 0.f;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -186,15 +215,15 @@ __device__ __forceinline__ void item_df32(const float (&s)[M], const unsigned ch
 }
 
 // Naive FP32 tier: Horner phase in seconds in FP32.
-template <bool MASKED>
-__device__ __forceinline__ void item_f32(const float (&s)[M], const unsigned char* cdata, const float* negA, int g,
+template <int CGV, bool MASKED>
+__device__ __forceinline__ void item_f32(const float (&s)[M], const unsigned char* cdata_g, const float* negA_g,
                                          int lane, int nvalid, int64_t tstart, float t0f, float hf,
-                                         float (&acc)[CG]) {
+                                         float (&acc)[CGV]) {
 #pragma unroll 1
-  for (int c = 0; c < CG; ++c) {
-    const float* k = reinterpret_cast<const float*>(cdata + (g * CG + c) * CAND_BYTES);
+  for (int c = 0; c < CGV; ++c) {
+    const float* k = reinterpret_cast<const float*>(cdata_g + c * CAND_BYTES);
     const float c0 = k[0], c1 = k[1], c2 = k[2], c3 = k[3];
-    const float nA = negA[g * CG + c];
+    const float nA = negA_g[c];
     float sum = 0.f;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -211,17 +240,24 @@ __device__ __forceinline__ void item_f32(const float (&s)[M], const unsigned cha
   }
 }
 
+// Items a warp evaluates per anchor batch (default tier).
+constexpr int IPB = 4;
+
 // Evaluate candidates [0, ncand) (prepared in cdata/negA/kexp, padded to npad,
-// a multiple of CG) on the CTA's tiles [tile_begin, tile_begin + ntiles_cta)
+// a multiple of CGV) on the CTA's tiles [tile_begin, tile_begin + ntiles_cta)
 // whose converted samples are s32 / s64 (indexed from tile_begin). Adds the
 // fixed-point partial SSE of each candidate into acc[cand] (shared).
-// anc: shared scratch for tiles_chunk x npad anchors. Ends with __syncthreads().
-template <int TIER>
+// Items (tile t, group g) = it, it = t * G + g, go to warps round-robin; for
+// the default tier each warp computes the tile anchors of its next IPB items
+// itself into its own slice of `anc` (IPB * CGV entries per warp), so no
+// CTA-wide barrier separates anchors from evaluation. Ends with __syncthreads().
+template <int TIER, int CGV>
 __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int ntiles_cta, const float* s32,
                            const double* s64, const unsigned char* cdata, const float* negA, const int* kexp,
-                           int ncand, int npad, uint4* anc, int tiles_chunk, unsigned long long* acc) {
+                           int ncand, int npad, uint4* anc, unsigned long long* acc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int G = npad / CG;
+  const int G = npad / CGV;
+  const int nitems = ntiles_cta * G;
   float kk[M], kkk[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
@@ -231,33 +267,42 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int ntiles_ct
   }
   const dfloat t0d = df_from_double(b.t0), hd = df_from_double(b.h);
   const float t0f = __double2float_rn(b.t0), hf = __double2float_rn(b.h);
+  uint4* anc_w = anc + warp * (IPB * CGV);
+  constexpr int LPC = 32 / CGV;  // lanes holding each candidate's warp sum
 
-  for (int cbeg = 0; cbeg < ntiles_cta; cbeg += tiles_chunk) {
-    const int nt = min(tiles_chunk, ntiles_cta - cbeg);
+  for (int base = warp; base < nitems; base += nw * IPB) {
     if (TIER == TIER_F64) {
-      for (int idx = tid; idx < nt * npad; idx += blockDim.x) {
-        const int t = idx / npad, c = idx - t * npad;
-        uint4 a = make_uint4(0, 0, 0, 0);
-        if (c < ncand) {
-          const u128* e = reinterpret_cast<const u128*>(cdata + c * CAND_BYTES);
-          Poly P;
-          P.e[0] = e[0];
-          P.e[1] = e[1];
-          P.e[2] = e[2];
-          P.e[3] = e[3];
-          a = make_anchor(P, (uint64_t)(tile_begin + cbeg + t) * (uint64_t)L);
+      for (int q = lane; q < IPB * CGV; q += 32) {
+        const int k = q / CGV, c = q - k * CGV;
+        const int it = base + k * nw;
+        uint4 av = make_uint4(0, 0, 0, 0);
+        if (it < nitems) {
+          const int t = it / G, cand = (it - t * G) * CGV + c;
+          if (cand < ncand) {
+            const u128* e = reinterpret_cast<const u128*>(cdata + cand * CAND_BYTES);
+            Poly P;
+            P.e[0] = e[0];
+            P.e[1] = e[1];
+            P.e[2] = e[2];
+            P.e[3] = e[3];
+            av = make_anchor(P, (uint64_t)(tile_begin + t) * (uint64_t)L);
+          }
         }
-        anc[idx] = a;
+        anc_w[q] = av;
       }
-      __syncthreads();
+      __syncwarp();
     }
-    for (int it = warp; it < nt * G; it += nw) {
+#pragma unroll 1
+    for (int k = 0; k < IPB; ++k) {
+      const int it = base + k * nw;
+      if (it >= nitems) break;
       const int t = it / G, g = it - t * G;
-      const int64_t tstart = (tile_begin + cbeg + t) * (int64_t)L;
+      const int64_t tstart = (tile_begin + t) * (int64_t)L;
       const int64_t rem = b.n - tstart;
       const int nvalid = rem < L ? (int)rem : L;
-      const int64_t soff = (int64_t)(cbeg + t) * L + lane * M;
-      int cand = g * CG + (lane >> 2);
+      const int64_t soff = (int64_t)t * L + lane * M;
+      const int cand = g * CGV + lane / LPC;
+      const bool owner = (lane & (LPC - 1)) == 0 && cand < ncand;
       if (TIER == TIER_PLAIN) {
         double s[M];
 #pragma unroll
@@ -266,12 +311,12 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int ntiles_ct
           s[m] = v.x;
           s[m + 1] = v.y;
         }
-        double acc8[CG];
-        if (nvalid == L) item_plain<false>(s, cdata, g, lane, nvalid, tstart, b, acc8);
-        else item_plain<true>(s, cdata, g, lane, nvalid, tstart, b, acc8);
-        const double z = warp_reduce_scatter8(acc8, lane);
-        if ((lane & 3) == 0 && cand < ncand) {
-          const long long v = __double2ll_rn(ldexp(z, kexp[cand]));
+        double accv[CGV];
+        if (nvalid == L) item_plain<CGV, false>(s, cdata + g * CGV * CAND_BYTES, lane, nvalid, tstart, b, accv);
+        else item_plain<CGV, true>(s, cdata + g * CGV * CAND_BYTES, lane, nvalid, tstart, b, accv);
+        const double z = warp_reduce_scatter<CGV>(accv, lane);
+        if (owner) {
+          const long long v = __double2ll_rn(z * __longlong_as_double((long long)(1023 + kexp[cand]) << 52));
           atomicAdd(&acc[cand], (unsigned long long)v);
         }
       } else {
@@ -284,27 +329,30 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int ntiles_ct
           s[m + 2] = v.z;
           s[m + 3] = v.w;
         }
-        float acc8[CG];
+        float accv[CGV];
+        const float* nA = negA + g * CGV;
+        const unsigned char* cd = cdata + g * CGV * CAND_BYTES;
         if (TIER == TIER_F64) {
-          const uint4* anc_t = anc + t * npad;
-          if (nvalid == L) item_f64<false>(s, anc_t, negA, g, lane, nvalid, kk, kkk, acc8);
-          else item_f64<true>(s, anc_t, negA, g, lane, nvalid, kk, kkk, acc8);
+          const uint4* anc_i = anc_w + k * CGV;
+          if (nvalid == L) item_f64<CGV, false>(s, anc_i, nA, lane, nvalid, kk, kkk, accv);
+          else item_f64<CGV, true>(s, anc_i, nA, lane, nvalid, kk, kkk, accv);
         } else if (TIER == TIER_DF32) {
-          if (nvalid == L) item_df32<false>(s, cdata, negA, g, lane, nvalid, tstart, t0d, hd, acc8);
-          else item_df32<true>(s, cdata, negA, g, lane, nvalid, tstart, t0d, hd, acc8);
+          if (nvalid == L) item_df32<CGV, false>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
+          else item_df32<CGV, true>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
         } else {
-          if (nvalid == L) item_f32<false>(s, cdata, negA, g, lane, nvalid, tstart, t0f, hf, acc8);
-          else item_f32<true>(s, cdata, negA, g, lane, nvalid, tstart, t0f, hf, acc8);
+          if (nvalid == L) item_f32<CGV, false>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
+          else item_f32<CGV, true>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
         }
-        const float z = warp_reduce_scatter8(acc8, lane);
-        if ((lane & 3) == 0 && cand < ncand) {
+        const float z = warp_reduce_scatter<CGV>(accv, lane);
+        if (owner) {
           const long long v = __float2ll_rn(z * exp2_int_f(kexp[cand]));
           atomicAdd(&acc[cand], (unsigned long long)v);
         }
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
+  __syncthreads();
 }
 
 // Stage tiles [tb, tb + nt) of the block into shared memory and convert them.
@@ -330,14 +378,15 @@ __device__ bool stage_tiles(const BlockArgs& b, int64_t tb, int nt, void* raw, f
 
 // Shared-memory carve-up common to both kernels.
 struct SmemLayout {
-  size_t off_mbar, off_cdata, off_negA, off_kexp, off_acc, off_anc, off_samp, off_raw, off_pop, total;
+  size_t off_mbar, off_cdata, off_negA, off_kexp, off_acc, off_draw, off_anc, off_samp, off_raw, off_pop, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// npad: padded candidates; tmax: max tiles per CTA; chunk: anchor tile chunk;
-// pop: population slots (0 for the objective kernel).
-__host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, int chunk, int esize, int pop) {
+// npad: padded candidates; tmax: max tiles per CTA; cgv: candidates per item;
+// pop: population slots (0 for the objective kernel); nthreads: CTA size.
+__host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, int cgv, int esize, int pop,
+                                                  int nthreads) {
   SmemLayout s;
   size_t o = 0;
   s.off_mbar = o;
@@ -352,8 +401,10 @@ __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, 
   o += align_up((size_t)npad * sizeof(int), 16);
   s.off_acc = o;
   o += align_up((size_t)npad * sizeof(unsigned long long), 16);
+  s.off_draw = o;
+  o += align_up((size_t)(pop ? 2 * npad : 0) * sizeof(uint32_t), 16);
   s.off_anc = o;
-  o += (tier == TIER_F64) ? (size_t)chunk * npad * sizeof(uint4) : 0;
+  o += (tier == TIER_F64) ? (size_t)(nthreads / 32) * IPB * cgv * sizeof(uint4) : 0;
   s.off_samp = o;
   o += align_up((size_t)tmax * L * (tier_uses_f64_samples(tier) ? 8 : 4), 128);
   s.off_raw = o;
@@ -377,14 +428,13 @@ struct ObjArgs {
   const double* cands;
   int ncand;
   int tpc;          // tiles per CTA (grid.x)
-  int cpc;          // candidates per CTA, multiple of CG (grid.y)
-  int tiles_chunk;
+  int cpc;          // candidates per CTA, multiple of the item width (grid.y)
   unsigned long long* acc;  // [ncand], zeroed by the caller
   int* err;
   uint64_t timeout_ns;
 };
 
-template <int TIER>
+template <int TIER, int CGV>
 __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int64_t tb = (int64_t)blockIdx.x * a.tpc;
@@ -392,8 +442,8 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   const int cb = blockIdx.y * a.cpc;
   const int nc = min(a.cpc, a.ncand - cb);
   if (nt <= 0 || nc <= 0) return;
-  const int npad = (nc + CG - 1) / CG * CG;
-  const SmemLayout S = smem_layout(TIER, npad, a.tpc, a.tiles_chunk, a.b.esize, 0);
+  const int npad = (nc + CGV - 1) / CGV * CGV;
+  const SmemLayout S = smem_layout(TIER, npad, a.tpc, CGV, a.b.esize, 0, NT);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S.off_mbar);
   unsigned char* cdata = smem + S.off_cdata;
   float* negA = reinterpret_cast<float*>(smem + S.off_negA);
@@ -405,28 +455,19 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   void* raw = smem + S.off_raw;
 
   const int tid = threadIdx.x;
-  if (tid < npad) {
-    acc[tid] = 0ull;
-    if (tid < nc) {
-      double th[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) th[j] = a.cands[(int64_t)(cb + tid) * D + j];
-      prep_candidate<TIER>(th, a.b, cdata + tid * CAND_BYTES, negA + tid, kexp + tid);
-    } else {
-      prep_zero(cdata + tid * CAND_BYTES, negA + tid, kexp + tid);
-    }
-  }
+  if (tid < npad) acc[tid] = 0ull;
+  prep_all<TIER>(a.cands + (int64_t)cb * D, nc, npad, a.b, cdata, negA, kexp, SSE_BITS_OBJ);
   if (!stage_tiles<TIER>(a.b, tb, nt, raw, s32, s64, mbar, a.timeout_ns, a.err)) return;
-  eval_range<TIER>(a.b, tb, nt, s32, s64, cdata, negA, kexp, nc, npad, anc, a.tiles_chunk, acc);
+  eval_range<TIER, CGV>(a.b, tb, nt, s32, s64, cdata, negA, kexp, nc, npad, anc, acc);
   if (tid < nc) atomicAdd(&a.acc[cb + tid], acc[tid]);
 }
 
-__global__ void k_finalize(const double* cands, int ncand, const unsigned long long* acc, int64_t n, double smax,
+__global__ void k_finalize(const double* cands, int ncand, const unsigned long long* acc, int64_t n, float smax_f,
                            double* sse) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncand) return;
-  const int k = sse_scale_exp(n, smax, cands[(int64_t)c * D]);
-  sse[c] = ldexp((double)(long long)acc[c], -k);
+  const int k = sse_scale_exp(n, smax_f, fabsf(__double2float_rn(cands[(int64_t)c * D])), SSE_BITS_OBJ);
+  sse[c] = fixed_to_double(acc[c], k);
 }
 
 struct DeArgs {
@@ -435,9 +476,7 @@ struct DeArgs {
   int np, npad, gens;
   int nctas;
   int tmax;
-  int tiles_chunk;
   unsigned long long* gacc;  // [3][npad], zeroed by the caller
-  unsigned* bar;             // arrival counter, zeroed by the caller
   int* err;                  // zeroed by the caller
   double* out;               // [6]
   double* pop_out;           // [np * 5] (device)
@@ -447,13 +486,16 @@ struct DeArgs {
 
 // Persistent DE solve: every CTA holds the whole population and generates
 // every trial itself (identical Philox draws, identical FP64 arithmetic), so
-// the only exchange is the per-generation fixed-point SSE sums, added with
-// global atomics into a 3-deep ring and read back after one grid barrier.
-// Launched cooperatively (all CTAs co-resident); every wait is bounded.
-template <int TIER>
+// the only exchange is the per-generation SSE of each trial. Each CTA adds
+// (partial << 8) | 1 to the trial's 64-bit word of a 3-deep ring: the low
+// byte counts arrivals, so a word whose low byte equals the CTA count holds
+// the complete fixed-point sum, and one acquire load per candidate replaces
+// a separate barrier, fence and read. Launched cooperatively (all CTAs
+// co-resident); every wait is bounded in time.
+template <int TIER, int CGV>
 __global__ void __launch_bounds__(NT, 1) k_de(DeArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const SmemLayout S = smem_layout(TIER, a.npad, a.tmax, a.tiles_chunk, a.b.esize, a.npad);
+  const SmemLayout S = smem_layout(TIER, a.npad, a.tmax, CGV, a.b.esize, a.npad, NT);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S.off_mbar);
   double* x = reinterpret_cast<double*>(smem + S.off_pop);
   double* u = x + a.npad * D;
@@ -462,6 +504,8 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeArgs a) {
   float* negA = reinterpret_cast<float*>(smem + S.off_negA);
   int* kexp = reinterpret_cast<int*>(smem + S.off_kexp);
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem + S.off_acc);
+  uint32_t* drp = reinterpret_cast<uint32_t*>(smem + S.off_draw);  // packed r1, r2, r3 of generation gen+1
+  uint32_t* drt = drp + a.npad;                                     // crossover masks of generation gen+1
   uint4* anc = reinterpret_cast<uint4*>(smem + S.off_anc);
   float* s32 = reinterpret_cast<float*>(smem + S.off_samp);
   double* s64 = reinterpret_cast<double*>(smem + S.off_samp);
@@ -469,73 +513,81 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeArgs a) {
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, bid = blockIdx.x;
+  const int np = a.np, npad = a.npad;
   const int64_t tb = (int64_t)bid * a.b.ntiles / a.nctas;
   const int nt = (int)((int64_t)(bid + 1) * a.b.ntiles / a.nctas - tb);
+  const unsigned long long arrived = (unsigned long long)(a.nctas & 0xff);
+  if (tid == 0) s_abort = 0;
   if (!stage_tiles<TIER>(a.b, tb, nt, raw, s32, s64, mbar, a.timeout_ns, a.err)) return;
 
   for (int gen = 0; gen <= a.gens; ++gen) {
     const int ring = gen % 3;
-    if (tid < a.npad) {
-      acc[tid] = 0ull;
-      if (tid < a.np) {
-        double* ui = u + tid * D;
-        if (gen == 0) de_init(a.dc, tid, ui);
-        else de_trial(a.dc, x, a.np, tid, (uint32_t)gen, ui);
-        prep_candidate<TIER>(ui, a.b, cdata + tid * CAND_BYTES, negA + tid, kexp + tid);
-      } else {
-        prep_zero(cdata + tid * CAND_BYTES, negA + tid, kexp + tid);
-      }
-    }
-    __syncthreads();
-    eval_range<TIER>(a.b, tb, nt, s32, s64, cdata, negA, kexp, a.np, a.npad, anc, a.tiles_chunk, acc);
-    if (tid < a.np) {
-      atomicAdd(&a.gacc[ring * a.npad + tid], acc[tid]);
-      // the slot of generation gen+1 was last read before barrier gen-1: clear it
-      if (bid == 0) a.gacc[((gen + 1) % 3) * a.npad + tid] = 0ull;
-    }
-    __syncthreads();
-    if (tid == 0) {
+    // the ring slot of generation gen+1 was last read before generation gen-1
+    // ended everywhere: CTA 0 clears it, and its fence orders the clear
+    // before its own contributions to this generation, which every reader
+    // acquires before contributing to generation gen+1
+    if (bid == 0 && tid < np) {
+      a.gacc[((gen + 1) % 3) * npad + tid] = 0ull;
       __threadfence();
-      atomicAdd(a.bar, 1u);
-      const unsigned target = (unsigned)(gen + 1) * (unsigned)a.nctas;
+    }
+    // trials u of this generation (the initial population at gen 0)
+    if (gen == 0) {
+      if (tid < np) de_init(a.dc, tid, u + tid * D);
+    } else {
+      for (int t = tid; t < D * npad; t += blockDim.x) {
+        const int j = t / npad, c = t - j * npad;
+        if (c < np) u[c * D + j] = de_component(a.dc, x, c, j, drp[c], drt[c]);
+      }
+    }
+    if (tid < npad) acc[tid] = 0ull;
+    __syncthreads();
+    prep_all<TIER>(u, np, npad, a.b, cdata, negA, kexp, SSE_BITS_DE);
+    eval_range<TIER, CGV>(a.b, tb, nt, s32, s64, cdata, negA, kexp, np, npad, anc, acc);
+    if (tid < np) {
+      unsigned long long* w = &a.gacc[ring * npad + tid];
+      atomicAdd(w, (acc[tid] << 8) | 1ull);
+      // wait for every CTA's contribution to this candidate, then select
       const uint64_t t_start = globaltimer_ns();
-      int abort = 0;
-      while (ld_acquire_u32(a.bar) < target) {
-        if (ld_volatile_i32(a.err) != DEV_OK) {
-          abort = 1;
-          break;
-        }
-        if (globaltimer_ns() - t_start > a.timeout_ns) {
-          atomicExch(a.err, DEV_TIMEOUT);
-          abort = 1;
-          break;
+      unsigned long long v;
+      int spins = 0;
+      while (((v = ld_acquire_u64(w)) & 0xffull) != arrived) {
+        if ((++spins & 63) == 0) {
+          if (ld_volatile_i32(a.err) != DEV_OK) {
+            s_abort = 1;
+            break;
+          }
+          if (globaltimer_ns() - t_start > a.timeout_ns) {
+            atomicExch(a.err, DEV_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
         }
       }
-      s_abort = abort;
-    }
-    __syncthreads();
-    if (s_abort) return;
-    if (tid < a.np) {
-      const unsigned long long v = __ldcg(&a.gacc[ring * a.npad + tid]);
-      const double f = ldexp((double)(long long)v, -kexp[tid]);
-      if (gen == 0 || f <= fx[tid]) {
+      const double f = fixed_to_double(v >> 8, kexp[tid]);
+      // SSE values are non-negative: their bit patterns order like the values
+      if (gen == 0 || __double_as_longlong(f) <= __double_as_longlong(fx[tid])) {
         fx[tid] = f;
 #pragma unroll
         for (int j = 0; j < D; ++j) x[tid * D + j] = u[tid * D + j];
       }
+    } else if (gen < a.gens && tid >= NP_MAX && tid < NP_MAX + np) {
+      // the next generation's draws do not depend on selection: overlap them with the wait
+      const int c = tid - NP_MAX;
+      de_draws(a.dc, np, c, (uint32_t)(gen + 1), &drp[c], &drt[c]);
     }
     __syncthreads();
+    if (s_abort) return;
   }
   if (bid == 0) {
     if (tid == 0) {
       int best = 0;
-      for (int i = 1; i < a.np; ++i)
-        if (fx[i] < fx[best]) best = i;
+      for (int i = 1; i < np; ++i)
+        if (__double_as_longlong(fx[i]) < __double_as_longlong(fx[best])) best = i;
       for (int j = 0; j < D; ++j) a.out[j] = x[best * D + j];
       a.out[D] = fx[best];
     }
-    for (int i = tid; i < a.np * D; i += blockDim.x) a.pop_out[i] = x[i];
-    for (int i = tid; i < a.np; i += blockDim.x) a.fit_out[i] = fx[i];
+    for (int i = tid; i < np * D; i += blockDim.x) a.pop_out[i] = x[i];
+    for (int i = tid; i < np; i += blockDim.x) a.fit_out[i] = fx[i];
   }
 }
 
