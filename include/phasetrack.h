@@ -145,6 +145,72 @@ PT_API int pt_de_solve(pt_ctx* ctx, const double* bounds, int pop, int gens, dou
 PT_API int pt_de_solve_ex(pt_ctx* ctx, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
                    uint32_t block_id, double* params_out, double* pop_out, double* fit_out, int tier);
 
+/* ---- Batched fits ---------------------------------------------------------
+ * Many independent blocks of uneven length, each with its own DE controls and
+ * population, solved in one persistent cooperative launch (replayed from a
+ * captured CUDA graph when the driver allows it). The paper fits its blocks
+ * one after another (Sec. 3.1.4, data process flow); a batch runs them
+ * concurrently. A block's result is bit-identical to pt_de_solve_ex on the
+ * same block alone: its sums of squares are exact integer sums of the same
+ * per-tile partials whatever CTAs evaluate them. */
+
+/* One block of a batch: the data block of Sec. 2.2 and the DE controls of
+ * Table 3-1-1 (meanings as in pt_load_block and pt_de_solve_ex). */
+typedef struct pt_block_spec {
+  const void* samples; /* host or device pointer, n values of type dtype; copied by pt_batch_create */
+  int64_t n;
+  int dtype;
+  double scale, fs, t0;
+  double bounds[10]; /* (lo, hi) for A, phi0, f0, f1, f2 */
+  int pop, gens;
+  double F, CR;
+  uint64_t seed;
+  uint32_t block_id;
+} pt_block_spec;
+
+/* Result of one fit: the best (A, phi0, f0, f1, f2) and its SSE. */
+typedef struct pt_fit {
+  double params[5];
+  double sse;
+} pt_fit;
+
+typedef struct pt_batch pt_batch;
+
+typedef struct pt_batch_info {
+  int nblocks;
+  int ngroups;      /* groups of CTAs working concurrently */
+  int group_ctas;   /* CTAs per group (per block in flight) */
+  int tier;
+  int uses_graph;   /* 1 if pt_batch_run replays a captured CUDA graph */
+  double sample_evals;  /* sum over blocks of n * pop * (gens + 1) */
+  double predicted_ms;  /* the autotuner's makespan estimate */
+  double last_ms;       /* device time of the last pt_batch_run */
+  double tune_rate;     /* calibrated objective sample-evals/s per CTA */
+  double tune_gen_us;   /* calibrated fixed cost per generation (us) */
+  double tune_sync_us;  /* calibrated extra cost per generation when a block spans CTAs (us) */
+} pt_batch_info;
+
+/* Copy the blocks to the device, choose the launch shape and capture it.
+ *   group_ctas  CTAs per block in flight; 0 lets the autotuner choose: it
+ *               calibrates the per-CTA rate and the per-generation costs on
+ *               the batch's first block (cached in the context) and picks the
+ *               group size whose longest-processing-time schedule of the
+ *               blocks over the groups has the shortest predicted makespan.
+ * Errors: PT_EINVAL, PT_ENOMEM, PT_ECUDA. *out is owned by the caller. */
+PT_API int pt_batch_create(pt_ctx* ctx, const pt_block_spec* specs, int nblocks, int tier, int group_ctas,
+                           pt_batch** out);
+
+/* Solve every block of the batch (synchronous). Errors: PT_ECUDA, PT_ETIMEOUT. */
+PT_API int pt_batch_run(pt_batch* batch);
+
+/* Copy the results of the last run: out holds nblocks entries (host pointer). */
+PT_API int pt_batch_results(pt_batch* batch, pt_fit* out);
+
+PT_API int pt_batch_get_info(const pt_batch* batch, pt_batch_info* info);
+
+/* Release the batch's device memory and graph. NULL is allowed. */
+PT_API void pt_batch_destroy(pt_batch* batch);
+
 /* Device time in milliseconds of the last pt_objective / pt_de_solve kernel
  * work, measured with CUDA events on the context's stream. */
 PT_API int pt_last_kernel_ms(const pt_ctx* ctx, float* ms);

@@ -186,3 +186,108 @@ class Context:
         v = ctypes.c_float()
         self._check(self._lib.pt_last_kernel_ms(self._h, ctypes.byref(v)))
         return float(v.value)
+
+
+# ---- batched fits ------------------------------------------------------------
+
+
+class BlockSpec(ctypes.Structure):
+    """Mirror of ``pt_block_spec``."""
+    _fields_ = [("samples", ctypes.c_void_p), ("n", ctypes.c_int64), ("dtype", ctypes.c_int),
+                ("scale", ctypes.c_double), ("fs", ctypes.c_double), ("t0", ctypes.c_double),
+                ("bounds", ctypes.c_double * 10), ("pop", ctypes.c_int), ("gens", ctypes.c_int),
+                ("F", ctypes.c_double), ("CR", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("block_id", ctypes.c_uint32)]
+
+
+class Fit(ctypes.Structure):
+    """Mirror of ``pt_fit``."""
+    _fields_ = [("params", ctypes.c_double * 5), ("sse", ctypes.c_double)]
+
+
+class BatchInfo(ctypes.Structure):
+    """Mirror of ``pt_batch_info``."""
+    _fields_ = [("nblocks", ctypes.c_int), ("ngroups", ctypes.c_int), ("group_ctas", ctypes.c_int),
+                ("tier", ctypes.c_int), ("uses_graph", ctypes.c_int), ("sample_evals", ctypes.c_double),
+                ("predicted_ms", ctypes.c_double), ("last_ms", ctypes.c_double), ("tune_rate", ctypes.c_double),
+                ("tune_gen_us", ctypes.c_double), ("tune_sync_us", ctypes.c_double)]
+
+
+def _batch_protos(lib):
+    if getattr(lib, "_batch_protos", False):
+        return
+    vp = ctypes.c_void_p
+    lib.pt_batch_create.argtypes = [vp, ctypes.POINTER(BlockSpec), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(vp)]
+    lib.pt_batch_create.restype = ctypes.c_int
+    lib.pt_batch_run.argtypes = [vp]
+    lib.pt_batch_run.restype = ctypes.c_int
+    lib.pt_batch_results.argtypes = [vp, ctypes.POINTER(Fit)]
+    lib.pt_batch_results.restype = ctypes.c_int
+    lib.pt_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+    lib.pt_batch_get_info.restype = ctypes.c_int
+    lib.pt_batch_destroy.argtypes = [vp]
+    lib.pt_batch_destroy.restype = None
+    lib._batch_protos = True
+
+
+class Batch:
+    """``pt_batch``: many blocks solved by one persistent launch.
+
+    ``blocks`` is a sequence of objects with ``samples`` (numpy), ``scale``,
+    ``fs``, ``t0``, ``bounds`` (5 x 2), ``pop``, ``gens``, ``F``, ``CR``,
+    ``de_seed`` and ``block_id`` attributes (e.g. ``synth.Block``)."""
+
+    def __init__(self, ctx: Context, blocks, tier: int = TIER_F64, group_ctas: int = 0):
+        self._ctx = ctx
+        self._lib = ctx._lib
+        _batch_protos(self._lib)
+        n = len(blocks)
+        specs = (BlockSpec * n)()
+        keep = []
+        for i, b in enumerate(blocks):
+            s = np.ascontiguousarray(b.samples)
+            keep.append(s)
+            sp = specs[i]
+            sp.samples = s.ctypes.data
+            sp.n = s.size
+            sp.dtype = _NP_TO_PT[s.dtype]
+            sp.scale, sp.fs, sp.t0 = float(b.scale), float(b.fs), float(b.t0)
+            bb = np.asarray(b.bounds, dtype=np.float64).reshape(-1)
+            for j in range(10):
+                sp.bounds[j] = float(bb[j])
+            sp.pop, sp.gens = int(b.pop), int(b.gens)
+            sp.F, sp.CR = float(b.F), float(b.CR)
+            sp.seed, sp.block_id = int(b.de_seed), int(b.block_id)
+        self._h = ctypes.c_void_p()
+        ctx._check(self._lib.pt_batch_create(ctx.handle, specs, n, int(tier), int(group_ctas), ctypes.byref(self._h)))
+        self.n = n
+
+    def run(self) -> float:
+        """Solve every block; returns the device time in ms."""
+        self._ctx._check(self._lib.pt_batch_run(self._h))
+        return self.info()["last_ms"]
+
+    def results(self):
+        """(params[n, 5], sse[n]) of the last run."""
+        out = (Fit * self.n)()
+        self._ctx._check(self._lib.pt_batch_results(self._h, out))
+        params = np.array([list(f.params) for f in out])
+        sse = np.array([f.sse for f in out])
+        return params, sse
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        self._ctx._check(self._lib.pt_batch_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def close(self):
+        if self._h:
+            self._lib.pt_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

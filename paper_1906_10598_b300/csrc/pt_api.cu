@@ -1,7 +1,8 @@
 // C ABI of the phase-tracking hot path (declarations and contracts in
-// include/phasetrack.h). Host side: argument validation, device buffers,
-// launch shapes and the synchronous call protocol. Every step of the
-// computation runs in the kernels of pt_kernels.cuh.
+// include/phasetrack.h): contexts, block loading, the objective and the DE
+// fit, plus the kernel launchers the batch and serving units share. Host side
+// only validates arguments, sizes buffers and shapes launches; every step of
+// the computation runs in the kernels of pt_kernels.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -9,59 +10,12 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
-#include "../../include/phasetrack.h"
+#include "pt_internal.h"
 #include "pt_kernels.cuh"
 
-using namespace pt;
-
-struct pt_ctx {
-  int device = 0;
-  int sms = 0;
-  size_t smem_optin = 0;
-  cudaStream_t own_stream = nullptr;
-  cudaStream_t stream = nullptr;
-  std::string err;
-  // loaded block
-  void* d_samples = nullptr;
-  size_t samples_cap = 0;
-  BlockArgs blk{};
-  bool has_block = false;
-  // objective scratch
-  unsigned long long* d_acc = nullptr;
-  size_t acc_cap = 0;
-  double* d_cands = nullptr;
-  size_t cands_cap = 0;
-  double* d_sse = nullptr;
-  size_t sse_cap = 0;
-  // DE scratch (sized for PT_POP_MAX)
-  unsigned long long* d_gacc = nullptr;
-  unsigned* d_bar = nullptr;
-  int* d_err = nullptr;
-  double* d_out = nullptr;
-  double* d_pop = nullptr;
-  double* d_fit = nullptr;
-  unsigned long long* d_u64 = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  float last_ms = 0.f;
-  uint64_t timeout_ns = 2000000000ull;
-};
-
-namespace {
-
-int fail(pt_ctx* c, int code, const std::string& msg) {
-  if (c) c->err = msg;
-  return code;
-}
-
-#define PT_CUDA(ctx, call)                                                                      \
-  do {                                                                                          \
-    cudaError_t e_ = (call);                                                                    \
-    if (e_ != cudaSuccess) {                                                                    \
-      return fail(ctx, e_ == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA,                  \
-                  std::string(#call) + ": " + cudaGetErrorString(e_));                          \
-    }                                                                                           \
-  } while (0)
+namespace pt {
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -85,27 +39,7 @@ int esize_of(int dtype) {
   }
 }
 
-template <typename T>
-int ensure(pt_ctx* c, T** p, size_t* cap, size_t count) {
-  if (*cap >= count) return PT_OK;
-  if (*p) cudaFree(*p);
-  *p = nullptr;
-  *cap = 0;
-  PT_CUDA(c, cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)));
-  *cap = count;
-  return PT_OK;
-}
-
 bool valid_tier(int t) { return t >= PT_TIER_F64 && t <= PT_TIER_F32; }
-
-int kernel_error(pt_ctx* c) {
-  int h_err = 0;
-  PT_CUDA(c, cudaMemcpyAsync(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  PT_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (h_err == DEV_TIMEOUT) return fail(c, PT_ETIMEOUT, "a bounded device-side wait expired");
-  if (h_err != DEV_OK) return fail(c, PT_ECUDA, "device error status " + std::to_string(h_err));
-  return PT_OK;
-}
 
 // Candidates per work item for the default tier: the width in {16, 8, 4}
 // that pads `n` the least (wider on ties); the other tiers use 8.
@@ -122,27 +56,58 @@ int pick_cg(int tier, int n) {
   return best;
 }
 
+namespace {
+
+template <typename T>
+int ensure(pt_ctx* c, T** p, size_t* cap, size_t count) {
+  if (*cap >= count) return PT_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  PT_CUDA(c, cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)));
+  *cap = count;
+  return PT_OK;
+}
+
+BlockArgs to_block_args(const HostBlock& h) {
+  BlockArgs b{};
+  b.samples = h.samples;
+  b.n = h.n;
+  b.ntiles = h.ntiles;
+  b.dtype = h.dtype;
+  b.esize = h.esize;
+  b.scale = h.scale;
+  b.smax = h.smax;
+  b.smax_f = (float)h.smax;
+  b.t0 = h.t0;
+  b.h = 1.0 / h.fs;
+  b.t0sq_2 = h.t0 * h.t0 / 2.0;
+  b.t0cu_6 = h.t0 * h.t0 * h.t0 / 6.0;
+  b.h2_2 = b.h * b.h / 2.0;
+  b.h3_6 = b.h * b.h * b.h / 6.0;
+  return b;
+}
+
 // ---- objective -------------------------------------------------------------
 
 template <int TIER, int CGV>
 int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
-  const BlockArgs& b = c->blk;
   ObjArgs a{};
-  a.b = b;
+  a.b = to_block_args(c->blk);
   a.cands = d_cands;
   a.ncand = ncand;
   a.cpc = std::min(((ncand + CGV - 1) / CGV) * CGV, NP_MAX);
   const int ny = (ncand + a.cpc - 1) / a.cpc;
   // about two CTAs per SM in total, tiles split evenly
   const int64_t want = 2LL * c->sms;
-  int64_t tpc = (b.ntiles * ny + want - 1) / want;
+  int64_t tpc = (a.b.ntiles * ny + want - 1) / want;
   tpc = std::max<int64_t>(1, std::min<int64_t>(tpc, 32));
   a.tpc = (int)tpc;
-  const int nx = (int)((b.ntiles + a.tpc - 1) / a.tpc);
+  const int nx = (int)((a.b.ntiles + a.tpc - 1) / a.tpc);
   a.acc = c->d_acc;
   a.err = c->d_err;
   a.timeout_ns = c->timeout_ns;
-  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, b.esize, 0, NT);
+  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, a.b.esize, 0, NT);
   if (S.total > c->smem_optin) return fail(c, PT_EINVAL, "objective launch needs too much shared memory");
   PT_CUDA(c, cudaFuncSetAttribute(k_objective<TIER, CGV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)S.total));
@@ -166,43 +131,175 @@ int launch_objective_any(pt_ctx* c, int tier, const double* d_cands, int ncand) 
   }
 }
 
-// ---- DE --------------------------------------------------------------------
+// ---- grouped DE --------------------------------------------------------------
 
-template <int TIER, int CGV>
-int launch_de(pt_ctx* c, DeArgs& a) {
-  const BlockArgs& b = c->blk;
-  a.npad = (a.np + CGV - 1) / CGV * CGV;
-  a.nctas = (int)std::min<int64_t>(b.ntiles, c->sms);
-  a.tmax = (int)((b.ntiles + a.nctas - 1) / a.nctas);
-  const SmemLayout S = smem_layout(TIER, a.npad, a.tmax, CGV, b.esize, a.npad, NT);
-  if (S.total > c->smem_optin)
-    return fail(c, PT_EINVAL, "block too long for the resident DE kernel (" + std::to_string(S.total) +
-                                  " bytes of shared memory per CTA)");
-  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, CGV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total));
+size_t smem_de(int tier, int sc_tiles, int esize_max) {
+  return smem_layout(tier, NP_MAX, sc_tiles, 16, esize_max, NP_MAX, NT).total;
+}
+
+template <int TIER>
+int launch_de_t(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
+  const size_t smem = smem_de(TIER, a.sc_tiles, a.esize_max);
+  if (smem > c->smem_optin) return fail(c, PT_EINVAL, "DE launch needs too much shared memory");
+  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, CGV>, NT, S.total));
-  if (occ < 1 || a.nctas > occ * c->sms) return fail(c, PT_EINVAL, "DE grid cannot be co-resident");
+  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER>, NT, smem));
+  const int grid = a.ngroups * a.k;
+  if (occ < 1 || grid > occ * c->sms) return fail(c, PT_EINVAL, "DE grid cannot be co-resident");
   void* args[] = {&a};
-  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, CGV>, dim3(a.nctas), dim3(NT), args, S.total,
-                                         c->stream));
+  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER>, dim3(grid), dim3(NT), args, smem, s));
   return PT_OK;
 }
 
-int launch_de_any(pt_ctx* c, int tier, DeArgs& a) {
-  switch (tier) {
-    case PT_TIER_F64: {
-      const int cg = pick_cg(tier, a.np);
-      if (cg == 16) return launch_de<TIER_F64, 16>(c, a);
-      if (cg == 8) return launch_de<TIER_F64, 8>(c, a);
-      return launch_de<TIER_F64, 4>(c, a);
+// Device layout of the descriptor buffer: blocks | sched | sched_off.
+size_t o_sched(int nblocks) { return align_up((size_t)nblocks * sizeof(DeBlockDesc), 256); }
+size_t o_off(int nblocks) { return o_sched(nblocks) + align_up((size_t)nblocks * sizeof(int), 256); }
+
+}  // namespace
+
+size_t de_desc_bytes(int nblocks, int ngroups) { return o_off(nblocks) + (size_t)(ngroups + 1) * sizeof(int); }
+
+int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want) {
+  int sc = (int)std::max<int64_t>(1, std::min<int64_t>(want, 96));
+  while (sc > 1 && smem_de(tier, sc, esize_max) > c->smem_optin) sc--;
+  return sc;
+}
+
+int load_samples(pt_ctx* c, cudaStream_t s, const void* samples, int64_t n, int dtype, double scale, double fs,
+                 double t0, void** dbuf, size_t* cap, unsigned long long* d_u64, HostBlock* hb) {
+  const int es = esize_of(dtype);
+  if (!samples || n < 1 || es == 0 || !(scale > 0.0) || !std::isfinite(scale) || !(fs > 0.0) ||
+      !std::isfinite(fs) || !std::isfinite(t0))
+    return fail(c, PT_EINVAL, "load: invalid argument");
+  if (n > (int64_t)1 << 36) return fail(c, PT_EINVAL, "load: block too long");
+  const int64_t ntiles = (n + L - 1) / L;
+  const size_t bytes = (size_t)ntiles * L * es;
+  if (*cap < bytes) {
+    if (*dbuf) cudaFree(*dbuf);
+    *dbuf = nullptr;
+    *cap = 0;
+    PT_CUDA(c, cudaMalloc(dbuf, bytes));
+    *cap = bytes;
+  }
+  const size_t nbytes = (size_t)n * es;
+  PT_CUDA(c, cudaMemcpyAsync(*dbuf, samples, nbytes, cudaMemcpyDefault, s));
+  if (bytes > nbytes) PT_CUDA(c, cudaMemsetAsync((char*)*dbuf + nbytes, 0, bytes - nbytes, s));
+  PT_CUDA(c, cudaMemsetAsync(d_u64, 0, sizeof(unsigned long long), s));
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4LL * c->sms);
+  k_absmax<<<grid, 256, 0, s>>>(*dbuf, n, dtype, d_u64);
+  PT_CUDA(c, cudaGetLastError());
+  unsigned long long bits = 0;
+  PT_CUDA(c, cudaMemcpyAsync(&bits, d_u64, sizeof(bits), cudaMemcpyDeviceToHost, s));
+  PT_CUDA(c, cudaStreamSynchronize(s));
+  double amax;
+  std::memcpy(&amax, &bits, sizeof(amax));
+  hb->samples = *dbuf;
+  hb->n = n;
+  hb->ntiles = ntiles;
+  hb->dtype = dtype;
+  hb->esize = es;
+  hb->scale = scale;
+  hb->smax = amax * scale;
+  hb->t0 = t0;
+  hb->fs = fs;
+  if (!std::isfinite(hb->smax)) return fail(c, PT_EINVAL, "load: non-finite samples");
+  return PT_OK;
+}
+
+int check_de_args(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, int tier) {
+  if (!bounds || pop < 4 || pop > PT_POP_MAX || gens < 0 || !valid_tier(tier) || !std::isfinite(F) ||
+      !std::isfinite(CR) || CR < 0.0)
+    return fail(c, PT_EINVAL, "DE: invalid argument");
+  if (is_device_ptr(bounds)) return fail(c, PT_EINVAL, "DE: bounds must be a host pointer");
+  for (int j = 0; j < D; ++j) {
+    const double lo = bounds[2 * j], hi = bounds[2 * j + 1];
+    if (!std::isfinite(lo) || !std::isfinite(hi) || lo > hi)
+      return fail(c, PT_EINVAL, "DE: bounds must be finite with lo <= hi");
+  }
+  return PT_OK;
+}
+
+}  // namespace pt
+
+namespace pt {
+
+int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blocks, int nblocks, const int* sched,
+                     const int* off, int ngroups, int k, void* d_desc_buf, unsigned long long* ring, int* d_err,
+                     int mode) {
+  std::vector<DeBlockDesc> desc(nblocks);
+  int esize_max = 1;
+  int64_t want = 1;
+  for (int i = 0; i < nblocks; ++i) {
+    const HostDeBlock& h = blocks[i];
+    DeBlockDesc& d = desc[i];
+    d.b = to_block_args(h.blk);
+    for (int j = 0; j < D; ++j) {
+      d.dc.lo[j] = h.lo[j];
+      d.dc.hi[j] = h.hi[j];
     }
-    case PT_TIER_PLAIN: return launch_de<TIER_PLAIN, 8>(c, a);
-    case PT_TIER_DF32: return launch_de<TIER_DF32, 8>(c, a);
-    default: return launch_de<TIER_F32, 8>(c, a);
+    d.dc.F = h.F;
+    d.dc.cr_all = h.CR >= 1.0;
+    d.dc.cr_thr = h.CR >= 1.0 ? 0xffffffffu : (uint32_t)(h.CR * 4294967296.0);
+    d.dc.periodic = (h.hi[1] - h.lo[1]) >= 2.0 * 3.14159265358979323846 * (1.0 - 1e-12);
+    d.dc.key = make_uint2((uint32_t)(h.seed & 0xffffffffu), (uint32_t)(h.seed >> 32));
+    d.dc.block_id = h.block_id;
+    d.np = h.pop;
+    d.gens = h.gens;
+    d.cg = pick_cg(tier, h.pop);
+    d.out = h.out;
+    d.pop_out = h.pop_out;
+    d.fit_out = h.fit_out;
+    esize_max = std::max(esize_max, h.blk.esize);
+    want = std::max<int64_t>(want, (h.blk.ntiles + k - 1) / k);
+  }
+  char* base = (char*)d_desc_buf;
+  if (mode & DE_UPLOAD) {
+    // pageable sources: each copy has consumed its source when it returns
+    PT_CUDA(c, cudaMemcpyAsync(base, desc.data(), nblocks * sizeof(DeBlockDesc), cudaMemcpyHostToDevice, s));
+    PT_CUDA(c, cudaMemcpyAsync(base + o_sched(nblocks), sched, nblocks * sizeof(int), cudaMemcpyHostToDevice, s));
+    PT_CUDA(c, cudaMemcpyAsync(base + o_off(nblocks), off, (ngroups + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  DeLaunch a{};
+  a.blocks = (const DeBlockDesc*)base;
+  a.sched = (const int*)(base + o_sched(nblocks));
+  a.sched_off = (const int*)(base + o_off(nblocks));
+  a.ngroups = ngroups;
+  a.k = k;
+  a.sc_tiles = pick_sc_tiles(c, tier, esize_max, want);
+  a.esize_max = esize_max;
+  a.ring = ring;
+  a.err = d_err;
+  a.timeout_ns = c->timeout_ns;
+  if (!(mode & DE_LAUNCH)) return PT_OK;
+  PT_CUDA(c, cudaMemsetAsync(ring, 0, (size_t)ngroups * 3 * NP_MAX * sizeof(unsigned long long), s));
+  PT_CUDA(c, cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  switch (tier) {
+    case PT_TIER_F64: return launch_de_t<TIER_F64>(c, s, a);
+    case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN>(c, s, a);
+    case PT_TIER_DF32: return launch_de_t<TIER_DF32>(c, s, a);
+    default: return launch_de_t<TIER_F32>(c, s, a);
   }
 }
 
-}  // namespace
+int launch_absmax(pt_ctx* c, cudaStream_t s, const void* dsamples, int64_t n, int dtype, unsigned long long* d_slot) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4LL * c->sms));
+  k_absmax<<<grid, 256, 0, s>>>(dsamples, n, dtype, d_slot);
+  PT_CUDA(c, cudaGetLastError());
+  return PT_OK;
+}
+
+int kernel_status(pt_ctx* c, cudaStream_t s, int* d_err) {
+  int h_err = 0;
+  PT_CUDA(c, cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PT_CUDA(c, cudaStreamSynchronize(s));
+  if (h_err == DEV_TIMEOUT) return fail(c, PT_ETIMEOUT, "a bounded device-side wait expired");
+  if (h_err != DEV_OK) return fail(c, PT_ECUDA, "device error status " + std::to_string(h_err));
+  return PT_OK;
+}
+
+}  // namespace pt
+
+using namespace pt;
 
 // ---- C ABI -------------------------------------------------------------------
 
@@ -231,25 +328,28 @@ int pt_create(pt_ctx** out, int device) {
   c->smem_optin = prop.sharedMemPerBlockOptin;
   if (bad(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking))) return PT_ECUDA;
   c->stream = c->own_stream;
-  if (bad(cudaMalloc(&c->d_gacc, 3 * PT_POP_MAX * sizeof(unsigned long long)))) return PT_ENOMEM;
-  if (bad(cudaMalloc(&c->d_bar, sizeof(unsigned)))) return PT_ENOMEM;
+  if (bad(cudaMalloc(&c->d_ring, (size_t)c->sms * 3 * NP_MAX * sizeof(unsigned long long)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_err, sizeof(int)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_out, 8 * sizeof(double)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_pop, PT_POP_MAX * D * sizeof(double)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_fit, PT_POP_MAX * sizeof(double)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_u64, sizeof(unsigned long long)))) return PT_ENOMEM;
+  if (bad(cudaMalloc(&c->d_desc, de_desc_bytes(1, 1)))) return PT_ENOMEM;
   if (bad(cudaEventCreate(&c->ev0))) return PT_ECUDA;
   if (bad(cudaEventCreate(&c->ev1))) return PT_ECUDA;
   *out = c;
   return PT_OK;
 }
 
+void pt_serve_shutdown(pt_ctx* c);  // pt_serve.cu
+
 void pt_destroy(pt_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  pt_serve_shutdown(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  void* bufs[] = {c->d_samples, c->d_acc, c->d_cands, c->d_sse, c->d_gacc, c->d_bar,
-                  c->d_err,     c->d_out, c->d_pop,   c->d_fit, c->d_u64};
+  void* bufs[] = {c->d_samples, c->d_acc, c->d_cands, c->d_sse, c->d_ring, c->d_err,
+                  c->d_out,     c->d_pop, c->d_fit,   c->d_u64, c->d_desc};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -276,51 +376,11 @@ int pt_last_kernel_ms(const pt_ctx* c, float* ms) {
 
 int pt_load_block(pt_ctx* c, const void* samples, int64_t n, int dtype, double scale, double fs, double t0) {
   if (!c) return PT_EINVAL;
-  const int es = esize_of(dtype);
-  if (!samples || n < 1 || es == 0 || !(scale > 0.0) || !std::isfinite(scale) || !(fs > 0.0) ||
-      !std::isfinite(fs) || !std::isfinite(t0))
-    return fail(c, PT_EINVAL, "pt_load_block: invalid argument");
-  if (n > (int64_t)1 << 36) return fail(c, PT_EINVAL, "pt_load_block: block too long");
   PT_CUDA(c, cudaSetDevice(c->device));
   c->has_block = false;
-  const int64_t ntiles = (n + L - 1) / L;
-  const size_t bytes = (size_t)ntiles * L * es;
-  if (c->samples_cap < bytes) {
-    if (c->d_samples) cudaFree(c->d_samples);
-    c->d_samples = nullptr;
-    c->samples_cap = 0;
-    PT_CUDA(c, cudaMalloc(&c->d_samples, bytes));
-    c->samples_cap = bytes;
-  }
-  const size_t nbytes = (size_t)n * es;
-  PT_CUDA(c, cudaMemcpyAsync(c->d_samples, samples, nbytes, cudaMemcpyDefault, c->stream));
-  if (bytes > nbytes)
-    PT_CUDA(c, cudaMemsetAsync((char*)c->d_samples + nbytes, 0, bytes - nbytes, c->stream));
-  PT_CUDA(c, cudaMemsetAsync(c->d_u64, 0, sizeof(unsigned long long), c->stream));
-  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4LL * c->sms);
-  k_absmax<<<grid, 256, 0, c->stream>>>(c->d_samples, n, dtype, c->d_u64);
-  PT_CUDA(c, cudaGetLastError());
-  unsigned long long bits = 0;
-  PT_CUDA(c, cudaMemcpyAsync(&bits, c->d_u64, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
-  PT_CUDA(c, cudaStreamSynchronize(c->stream));
-  double amax;
-  std::memcpy(&amax, &bits, sizeof(amax));
-  BlockArgs& b = c->blk;
-  b.samples = c->d_samples;
-  b.n = n;
-  b.ntiles = ntiles;
-  b.dtype = dtype;
-  b.esize = es;
-  b.scale = scale;
-  b.smax = amax * scale;
-  b.smax_f = (float)b.smax;
-  if (!std::isfinite(b.smax)) return fail(c, PT_EINVAL, "pt_load_block: non-finite samples");
-  b.t0 = t0;
-  b.h = 1.0 / fs;
-  b.t0sq_2 = t0 * t0 / 2.0;
-  b.t0cu_6 = t0 * t0 * t0 / 6.0;
-  b.h2_2 = b.h * b.h / 2.0;
-  b.h3_6 = b.h * b.h * b.h / 6.0;
+  const int rc = load_samples(c, c->stream, samples, n, dtype, scale, fs, t0, &c->d_samples, &c->samples_cap,
+                              c->d_u64, &c->blk);
+  if (rc != PT_OK) return rc;
   c->has_block = true;
   return PT_OK;
 }
@@ -348,12 +408,13 @@ int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int
   PT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   rc = launch_objective_any(c, tier, d_c, (int)n);
   if (rc != PT_OK) return rc;
-  k_finalize<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(d_c, (int)n, c->d_acc, c->blk.n, c->blk.smax_f, d_out);
+  k_finalize<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(d_c, (int)n, c->d_acc, c->blk.n, (float)c->blk.smax,
+                                                             d_out);
   PT_CUDA(c, cudaGetLastError());
   PT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   if (!dev_out)
     PT_CUDA(c, cudaMemcpyAsync(sse_out, d_out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  if ((rc = kernel_error(c)) != PT_OK) return rc;
+  if ((rc = kernel_status(c, c->stream, c->d_err)) != PT_OK) return rc;
   PT_CUDA(c, cudaEventElapsedTime(&c->last_ms, c->ev0, c->ev1));
   return PT_OK;
 }
@@ -361,44 +422,34 @@ int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int
 int pt_de_solve_ex(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
                    uint32_t block_id, double* params_out, double* pop_out, double* fit_out, int tier) {
   if (!c) return PT_EINVAL;
-  if (!bounds || !params_out || pop < 4 || pop > PT_POP_MAX || gens < 0 || !valid_tier(tier) ||
-      !std::isfinite(F) || !std::isfinite(CR) || CR < 0.0)
-    return fail(c, PT_EINVAL, "pt_de_solve: invalid argument");
-  if (is_device_ptr(bounds)) return fail(c, PT_EINVAL, "pt_de_solve: bounds must be a host pointer");
-  for (int j = 0; j < D; ++j) {
-    const double lo = bounds[2 * j], hi = bounds[2 * j + 1];
-    if (!std::isfinite(lo) || !std::isfinite(hi) || lo > hi)
-      return fail(c, PT_EINVAL, "pt_de_solve: bounds must be finite with lo <= hi");
-  }
+  int rc = check_de_args(c, bounds, pop, gens, F, CR, tier);
+  if (rc != PT_OK) return rc;
+  if (!params_out) return fail(c, PT_EINVAL, "pt_de_solve: params_out is null");
   if (!c->has_block) return fail(c, PT_ENOBLOCK, "pt_de_solve: no block loaded");
   PT_CUDA(c, cudaSetDevice(c->device));
-  DeArgs a{};
-  a.b = c->blk;
+  HostDeBlock h;
+  h.blk = c->blk;
   for (int j = 0; j < D; ++j) {
-    a.dc.lo[j] = bounds[2 * j];
-    a.dc.hi[j] = bounds[2 * j + 1];
+    h.lo[j] = bounds[2 * j];
+    h.hi[j] = bounds[2 * j + 1];
   }
-  a.dc.F = F;
-  a.dc.cr_all = CR >= 1.0;
-  a.dc.cr_thr = CR >= 1.0 ? 0xffffffffu : (uint32_t)(CR * 4294967296.0);
-  a.dc.periodic = (bounds[3] - bounds[2]) >= 2.0 * 3.14159265358979323846 * (1.0 - 1e-12);
-  a.dc.key = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
-  a.dc.block_id = block_id;
-  a.np = pop;
-  a.gens = gens;
-  a.gacc = c->d_gacc;
-  a.err = c->d_err;
-  a.out = c->d_out;
-  a.pop_out = c->d_pop;
-  a.fit_out = c->d_fit;
-  a.timeout_ns = c->timeout_ns;
-  PT_CUDA(c, cudaMemsetAsync(c->d_gacc, 0, 3 * PT_POP_MAX * sizeof(unsigned long long), c->stream));
-  PT_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  h.pop = pop;
+  h.gens = gens;
+  h.F = F;
+  h.CR = CR;
+  h.seed = seed;
+  h.block_id = block_id;
+  h.out = c->d_out;
+  h.pop_out = c->d_pop;
+  h.fit_out = c->d_fit;
+  const int sched[1] = {0}, off[2] = {0, 1};
+  const int k = (int)std::min<int64_t>(c->blk.ntiles, c->sms);
   PT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-  int rc = launch_de_any(c, tier, a);
+  rc = launch_de_groups(c, c->stream, tier, &h, 1, sched, off, 1, k, c->d_desc, c->d_ring, c->d_err,
+                        DE_UPLOAD | DE_LAUNCH);
   if (rc != PT_OK) return rc;
   PT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
-  if ((rc = kernel_error(c)) != PT_OK) return rc;
+  if ((rc = kernel_status(c, c->stream, c->d_err)) != PT_OK) return rc;
   PT_CUDA(c, cudaEventElapsedTime(&c->last_ms, c->ev0, c->ev1));
   PT_CUDA(c, cudaMemcpyAsync(params_out, c->d_out, (D + 1) * sizeof(double), cudaMemcpyDefault, c->stream));
   if (pop_out)

@@ -1,0 +1,355 @@
+// Batched DE fits (pt_batch_*): many independent blocks, one persistent
+// cooperative launch over groups of CTAs, replayed from a captured CUDA graph.
+//
+// Autotuner: the per-generation time of one block on k CTAs is modelled as
+//   t(k) = ceil(ntiles / k) * 256 * npad / R + c_gen + [k > 1] c_sync,
+// with R the objective rate of one CTA, c_gen the fixed per-generation cost
+// (trial generation, FP64 set-up, selection) and c_sync the extra cost of the
+// cross-CTA exchange. R, c_gen and c_sync are calibrated with short DE runs on
+// the batch's first block and cached in the context. For each candidate group
+// size k the blocks are assigned longest-first to the least-loaded of the
+// floor(SMs / k) groups (LPT); the k with the shortest predicted makespan wins.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <vector>
+
+#include "pt_internal.h"
+
+using namespace pt;
+
+struct pt_batch {
+  pt_ctx* ctx = nullptr;
+  int tier = 0;
+  int nblocks = 0;
+  int ngroups = 0, k = 0;
+  double predicted_ms = 0.0, sample_evals = 0.0;
+  float last_ms = 0.f;
+  void* d_arena = nullptr;          // all blocks' samples, each padded to a whole tile
+  unsigned long long* d_amax = nullptr;
+  double* d_out = nullptr;          // nblocks x 6
+  void* d_desc = nullptr;           // descriptors + schedule
+  unsigned long long* d_ring = nullptr;
+  int* d_err = nullptr;
+  std::vector<HostDeBlock> blocks;
+  std::vector<int> sched, off;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int64_t padded_bytes(int64_t n, int esize) { return (n + HOST_L - 1) / HOST_L * HOST_L * esize; }
+
+// Per-generation seconds of one DE run of `b` on k CTAs: time two runs that
+// differ only in the generation count and difference them.
+int time_per_gen(pt_ctx* c, int tier, HostDeBlock b, int k, double* out) {
+  const int sched[1] = {0}, off[2] = {0, 1};
+  float ms[2];
+  const int gens[2] = {4, 16};
+  for (int r = 0; r < 2; ++r) {
+    b.gens = gens[r];
+    b.out = c->d_out;
+    b.pop_out = nullptr;
+    b.fit_out = nullptr;
+    PT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+    int rc = launch_de_groups(c, c->stream, tier, &b, 1, sched, off, 1, k, c->d_desc, c->d_ring, c->d_err,
+                              DE_UPLOAD | DE_LAUNCH);
+    if (rc != PT_OK) return rc;
+    PT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+    if ((rc = kernel_status(c, c->stream, c->d_err)) != PT_OK) return rc;
+    PT_CUDA(c, cudaEventElapsedTime(&ms[r], c->ev0, c->ev1));
+  }
+  *out = std::max(1e-9, (ms[1] - ms[0]) * 1e-3 / (gens[1] - gens[0]));
+  return PT_OK;
+}
+
+int npad_of(int tier, int pop) {
+  const int cg = pick_cg(tier, pop);
+  return (pop + cg - 1) / cg * cg;
+}
+
+// Calibrate R, c_gen, c_sync (cached in the context per tier-independent rates).
+int calibrate(pt_ctx* c, int tier, const HostDeBlock& b0) {
+  if (c->tuned) return PT_OK;
+  HostDeBlock b = b0;
+  const int64_t nt = b.blk.ntiles;
+  double t_full, t_small, t_k;
+  int rc;
+  if ((rc = time_per_gen(c, tier, b, 1, &t_full)) != PT_OK) return rc;
+  HostDeBlock bs = b;
+  bs.pop = 8;
+  if ((rc = time_per_gen(c, tier, bs, 1, &t_small)) != PT_OK) return rc;
+  const int kk = (int)std::min<int64_t>(4, nt);
+  if ((rc = time_per_gen(c, tier, b, kk, &t_k)) != PT_OK) return rc;
+  const double W = (double)nt * HOST_L;
+  const double dn = (double)(npad_of(tier, b.pop) - npad_of(tier, 8));
+  double R = dn > 0 && t_full > t_small ? W * dn / (t_full - t_small) : W * npad_of(tier, b.pop) / t_full;
+  double cg = std::max(0.0, t_full - W * npad_of(tier, b.pop) / R);
+  const double Wk = (double)((nt + kk - 1) / kk) * HOST_L;
+  double cs = std::max(0.0, t_k - (Wk * npad_of(tier, b.pop) / R + cg));
+  c->tune_rate = R;
+  c->tune_fixed_s = cg;
+  c->tune_sync_s = cs;
+  c->tuned = true;
+  return PT_OK;
+}
+
+double block_seconds(const pt_ctx* c, int tier, const HostDeBlock& b, int k) {
+  const double W = (double)((b.blk.ntiles + k - 1) / k) * HOST_L;
+  const double per_gen = W * npad_of(tier, b.pop) / c->tune_rate + c->tune_fixed_s + (k > 1 ? c->tune_sync_s : 0.0);
+  return per_gen * (b.gens + 1);
+}
+
+// Longest-processing-time assignment of blocks to `ng` groups; returns makespan.
+double lpt(const std::vector<double>& t, int ng, std::vector<int>* sched, std::vector<int>* off) {
+  std::vector<int> order(t.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return t[a] > t[b]; });
+  typedef std::pair<double, int> Load;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+  for (int g = 0; g < ng; ++g) pq.push({0.0, g});
+  std::vector<std::vector<int>> lists(ng);
+  for (int i : order) {
+    Load l = pq.top();
+    pq.pop();
+    lists[l.second].push_back(i);
+    pq.push({l.first + t[i], l.second});
+  }
+  double makespan = 0.0;
+  while (!pq.empty()) {
+    makespan = std::max(makespan, pq.top().first);
+    pq.pop();
+  }
+  if (sched && off) {
+    sched->clear();
+    off->assign(1, 0);
+    for (auto& l : lists) {
+      sched->insert(sched->end(), l.begin(), l.end());
+      off->push_back((int)sched->size());
+    }
+  }
+  return makespan;
+}
+
+void release(pt_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  void* bufs[] = {b->d_arena, b->d_amax, b->d_out, b->d_desc, b->d_ring, b->d_err};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier, int group_ctas, pt_batch** out) {
+  if (!c) return PT_EINVAL;
+  if (!out || !specs || nblocks < 1 || !valid_tier(tier) || group_ctas < 0)
+    return fail(c, PT_EINVAL, "pt_batch_create: invalid argument");
+  *out = nullptr;
+  PT_CUDA(c, cudaSetDevice(c->device));
+  int rc;
+  for (int i = 0; i < nblocks; ++i) {
+    const pt_block_spec& s = specs[i];
+    if ((rc = check_de_args(c, s.bounds, s.pop, s.gens, s.F, s.CR, tier)) != PT_OK) return rc;
+    if (!s.samples || s.n < 1 || esize_of(s.dtype) == 0 || !(s.scale > 0.0) || !(s.fs > 0.0) ||
+        !std::isfinite(s.t0) || !std::isfinite(s.scale) || !std::isfinite(s.fs))
+      return fail(c, PT_EINVAL, "pt_batch_create: invalid block " + std::to_string(i));
+  }
+  pt_batch* b = new (std::nothrow) pt_batch();
+  if (!b) return PT_ENOMEM;
+  b->ctx = c;
+  b->tier = tier;
+  b->nblocks = nblocks;
+  auto bail = [&](int code) {
+    release(b);
+    return code;
+  };
+  // one arena for every block's samples, each padded with zeros to whole tiles
+  std::vector<int64_t> offs(nblocks);
+  int64_t total = 0;
+  for (int i = 0; i < nblocks; ++i) {
+    offs[i] = total;
+    total += (padded_bytes(specs[i].n, esize_of(specs[i].dtype)) + 255) / 256 * 256;
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->d_arena, total)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_amax, nblocks * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_out, (size_t)nblocks * 6 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_err, sizeof(int))) != cudaSuccess || (e = cudaEventCreate(&b->ev0)) != cudaSuccess ||
+      (e = cudaEventCreate(&b->ev1)) != cudaSuccess) {
+    fail(c, e == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA,
+         std::string("pt_batch_create: ") + cudaGetErrorString(e));
+    return bail(e == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA);
+  }
+  cudaStream_t s = c->stream;
+  if (cudaMemsetAsync(b->d_arena, 0, total, s) != cudaSuccess ||
+      cudaMemsetAsync(b->d_amax, 0, nblocks * sizeof(unsigned long long), s) != cudaSuccess)
+    return bail(fail(c, PT_ECUDA, "pt_batch_create: memset failed"));
+  for (int i = 0; i < nblocks; ++i) {
+    const pt_block_spec& sp = specs[i];
+    char* dst = (char*)b->d_arena + offs[i];
+    if (cudaMemcpyAsync(dst, sp.samples, (size_t)sp.n * esize_of(sp.dtype), cudaMemcpyDefault, s) != cudaSuccess)
+      return bail(fail(c, PT_ECUDA, "pt_batch_create: sample copy failed"));
+    if ((rc = launch_absmax(c, s, dst, sp.n, sp.dtype, b->d_amax + i)) != PT_OK) return bail(rc);
+  }
+  std::vector<unsigned long long> amax(nblocks);
+  if (cudaMemcpyAsync(amax.data(), b->d_amax, nblocks * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return bail(fail(c, PT_ECUDA, "pt_batch_create: absmax failed"));
+  b->blocks.resize(nblocks);
+  for (int i = 0; i < nblocks; ++i) {
+    const pt_block_spec& sp = specs[i];
+    HostDeBlock& h = b->blocks[i];
+    double a;
+    std::memcpy(&a, &amax[i], sizeof(a));
+    h.blk.samples = (char*)b->d_arena + offs[i];
+    h.blk.n = sp.n;
+    h.blk.ntiles = (sp.n + HOST_L - 1) / HOST_L;
+    h.blk.dtype = sp.dtype;
+    h.blk.esize = esize_of(sp.dtype);
+    h.blk.scale = sp.scale;
+    h.blk.smax = a * sp.scale;
+    h.blk.t0 = sp.t0;
+    h.blk.fs = sp.fs;
+    for (int j = 0; j < HOST_D; ++j) {
+      h.lo[j] = sp.bounds[2 * j];
+      h.hi[j] = sp.bounds[2 * j + 1];
+    }
+    h.pop = sp.pop;
+    h.gens = sp.gens;
+    h.F = sp.F;
+    h.CR = sp.CR;
+    h.seed = sp.seed;
+    h.block_id = sp.block_id;
+    h.out = b->d_out + (size_t)i * 6;
+    b->sample_evals += (double)sp.n * sp.pop * (sp.gens + 1);
+  }
+  // launch shape
+  if ((rc = calibrate(c, tier, b->blocks[0])) != PT_OK) return bail(rc);
+  std::vector<int> ks;
+  if (group_ctas > 0) ks.push_back(std::min(group_ctas, c->sms));
+  else
+    for (int k : {1, 2, 4, 8, 16, 37, 74})
+      if (k <= c->sms) ks.push_back(k);
+  double best = 1e300;
+  for (int k : ks) {
+    std::vector<double> t(nblocks);
+    for (int i = 0; i < nblocks; ++i) t[i] = block_seconds(c, tier, b->blocks[i], k);
+    const int ng = std::min(c->sms / k, nblocks);
+    const double m = lpt(t, ng, nullptr, nullptr);
+    if (m < best) {
+      best = m;
+      b->k = k;
+      b->ngroups = ng;
+    }
+  }
+  {
+    std::vector<double> t(nblocks);
+    for (int i = 0; i < nblocks; ++i) t[i] = block_seconds(c, tier, b->blocks[i], b->k);
+    lpt(t, b->ngroups, &b->sched, &b->off);
+  }
+  b->predicted_ms = best * 1e3;
+  if ((e = cudaMalloc(&b->d_desc, de_desc_bytes(nblocks, b->ngroups))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_ring, (size_t)b->ngroups * 3 * HOST_NP_MAX * sizeof(unsigned long long))) !=
+          cudaSuccess)
+    return bail(fail(c, PT_ENOMEM, "pt_batch_create: descriptor allocation failed"));
+  if ((rc = launch_de_groups(c, s, tier, b->blocks.data(), nblocks, b->sched.data(), b->off.data(), b->ngroups,
+                             b->k, b->d_desc, b->d_ring, b->d_err, DE_UPLOAD)) != PT_OK)
+    return bail(rc);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(c, PT_ECUDA, "pt_batch_create: upload failed"));
+  // capture the launch (ring/error clears + cooperative kernel) as a graph;
+  // if the driver refuses, pt_batch_run launches directly
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const int lr = launch_de_groups(c, cs, tier, b->blocks.data(), nblocks, b->sched.data(), b->off.data(),
+                                      b->ngroups, b->k, b->d_desc, b->d_ring, b->d_err, DE_LAUNCH);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+      ok = lr == PT_OK && ee == cudaSuccess && g != nullptr;
+      if (ok && cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+        b->graph = g;
+      } else {
+        if (g) cudaGraphDestroy(g);
+        b->exec = nullptr;
+      }
+    }
+    cudaGetLastError();
+    cudaStreamDestroy(cs);
+    c->err.clear();
+  }
+  *out = b;
+  return PT_OK;
+}
+
+int pt_batch_run(pt_batch* b) {
+  if (!b) return PT_EINVAL;
+  pt_ctx* c = b->ctx;
+  PT_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  PT_CUDA(c, cudaEventRecord(b->ev0, s));
+  if (b->exec) {
+    PT_CUDA(c, cudaGraphLaunch(b->exec, s));
+  } else {
+    const int rc = launch_de_groups(c, s, b->tier, b->blocks.data(), b->nblocks, b->sched.data(), b->off.data(),
+                                    b->ngroups, b->k, b->d_desc, b->d_ring, b->d_err, DE_LAUNCH);
+    if (rc != PT_OK) return rc;
+  }
+  PT_CUDA(c, cudaEventRecord(b->ev1, s));
+  const int rc = kernel_status(c, s, b->d_err);
+  if (rc != PT_OK) return rc;
+  PT_CUDA(c, cudaEventElapsedTime(&b->last_ms, b->ev0, b->ev1));
+  return PT_OK;
+}
+
+int pt_batch_results(pt_batch* b, pt_fit* out) {
+  if (!b || !out) return PT_EINVAL;
+  pt_ctx* c = b->ctx;
+  std::vector<double> h((size_t)b->nblocks * 6);
+  PT_CUDA(c, cudaMemcpyAsync(h.data(), b->d_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PT_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < b->nblocks; ++i) {
+    for (int j = 0; j < 5; ++j) out[i].params[j] = h[(size_t)i * 6 + j];
+    out[i].sse = h[(size_t)i * 6 + 5];
+  }
+  return PT_OK;
+}
+
+int pt_batch_get_info(const pt_batch* b, pt_batch_info* info) {
+  if (!b || !info) return PT_EINVAL;
+  info->nblocks = b->nblocks;
+  info->ngroups = b->ngroups;
+  info->group_ctas = b->k;
+  info->tier = b->tier;
+  info->uses_graph = b->exec ? 1 : 0;
+  info->sample_evals = b->sample_evals;
+  info->predicted_ms = b->predicted_ms;
+  info->last_ms = b->last_ms;
+  info->tune_rate = b->ctx->tune_rate;
+  info->tune_gen_us = b->ctx->tune_fixed_s * 1e6;
+  info->tune_sync_us = b->ctx->tune_sync_s * 1e6;
+  return PT_OK;
+}
+
+void pt_batch_destroy(pt_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->ctx->device);
+  cudaStreamSynchronize(b->ctx->stream);
+  release(b);
+}
+
+}  // extern "C"

@@ -370,6 +370,8 @@ __device__ __forceinline__ bool bulk_stage(void* dst, const void* src, uint32_t 
           : "memory");
       if (done) {
         ok = 1;
+        // the phase completed: invalidate so the next staging can re-initialise it
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
         break;
       }
       if (globaltimer_ns() - t_start > timeout_ns) break;

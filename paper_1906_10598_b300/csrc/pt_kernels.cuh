@@ -470,82 +470,102 @@ __global__ void k_finalize(const double* cands, int ncand, const unsigned long l
   sse[c] = fixed_to_double(acc[c], k);
 }
 
-struct DeArgs {
+// One block's DE problem (device-side descriptor).
+struct DeBlockDesc {
   BlockArgs b;
   DeControls dc;
-  int np, npad, gens;
-  int nctas;
-  int tmax;
-  unsigned long long* gacc;  // [3][npad], zeroed by the caller
+  int np, gens;
+  int cg;            // candidates per work item for this block (16, 8 or 4)
+  double* out;       // [6] device: best params + SSE
+  double* pop_out;   // [np * 5] device or nullptr
+  double* fit_out;   // [np] device or nullptr
+};
+
+// A persistent DE launch: `ngroups` groups of `k` co-resident CTAs; group q
+// solves blocks sched[sched_off[q] .. sched_off[q+1]) in order.
+struct DeLaunch {
+  const DeBlockDesc* blocks;
+  const int* sched;
+  const int* sched_off;
+  int ngroups, k;
+  int sc_tiles;              // tiles staged per CTA at a time (shared-memory budget)
+  int esize_max;             // largest sample size in the launch (shared-memory layout)
+  unsigned long long* ring;  // [ngroups][3][NP_MAX], zeroed by the caller
   int* err;                  // zeroed by the caller
-  double* out;               // [6]
-  double* pop_out;           // [np * 5] (device)
-  double* fit_out;           // [np] (device)
   uint64_t timeout_ns;
 };
 
-// Persistent DE solve: every CTA holds the whole population and generates
-// every trial itself (identical Philox draws, identical FP64 arithmetic), so
-// the only exchange is the per-generation SSE of each trial. Each CTA adds
-// (partial << 8) | 1 to the trial's 64-bit word of a 3-deep ring: the low
-// byte counts arrivals, so a word whose low byte equals the CTA count holds
-// the complete fixed-point sum, and one acquire load per candidate replaces
-// a separate barrier, fence and read. Launched cooperatively (all CTAs
-// co-resident); every wait is bounded in time.
+struct DeSmem {
+  uint64_t* mbar;
+  double *x, *u, *fx;
+  unsigned char* cdata;
+  float* negA;
+  int* kexp;
+  unsigned long long* acc;
+  uint32_t *drp, *drt;
+  uint4* anc;
+  float* s32;
+  double* s64;
+  void* raw;
+};
+
+// DE/rand/1/bin on one block by `k` CTAs (this one is `rank`). Every CTA holds
+// the whole population and generates every trial itself (identical Philox
+// draws, identical FP64 arithmetic), so the only exchange is each trial's SSE:
+// every CTA adds (partial << 8) | 1 to the trial's 64-bit word of the group's
+// 3-deep ring, whose low byte counts arrivals; a word whose low byte equals k
+// holds the complete fixed-point sum, and one acquire load per candidate
+// replaces a barrier, a fence and a separate read. `gg` counts the group's
+// generations across blocks so the ring discipline continues from block to
+// block. Returns false if a bounded wait expired or another CTA failed.
 template <int TIER, int CGV>
-__global__ void __launch_bounds__(NT, 1) k_de(DeArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const SmemLayout S = smem_layout(TIER, a.npad, a.tmax, CGV, a.b.esize, a.npad, NT);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S.off_mbar);
-  double* x = reinterpret_cast<double*>(smem + S.off_pop);
-  double* u = x + a.npad * D;
-  double* fx = u + a.npad * D;
-  unsigned char* cdata = smem + S.off_cdata;
-  float* negA = reinterpret_cast<float*>(smem + S.off_negA);
-  int* kexp = reinterpret_cast<int*>(smem + S.off_kexp);
-  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem + S.off_acc);
-  uint32_t* drp = reinterpret_cast<uint32_t*>(smem + S.off_draw);  // packed r1, r2, r3 of generation gen+1
-  uint32_t* drt = drp + a.npad;                                     // crossover masks of generation gen+1
-  uint4* anc = reinterpret_cast<uint4*>(smem + S.off_anc);
-  float* s32 = reinterpret_cast<float*>(smem + S.off_samp);
-  double* s64 = reinterpret_cast<double*>(smem + S.off_samp);
-  void* raw = smem + S.off_raw;
-  __shared__ int s_abort;
+__device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long long* ring, unsigned long long& gg,
+                         const DeSmem& sm, const DeLaunch& a, int* s_abort) {
+  const int tid = threadIdx.x;
+  const int np = d.np, npad = (d.np + CGV - 1) / CGV * CGV;
+  const BlockArgs& b = d.b;
+  const int64_t tb = (int64_t)rank * b.ntiles / k;
+  const int nt = (int)((int64_t)(rank + 1) * b.ntiles / k - tb);
+  const bool resident = nt <= a.sc_tiles;
+  const unsigned long long arrived = (unsigned long long)(k & 0xff);
+  if (resident && nt > 0 && !stage_tiles<TIER>(b, tb, nt, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err))
+    return false;
 
-  const int tid = threadIdx.x, bid = blockIdx.x;
-  const int np = a.np, npad = a.npad;
-  const int64_t tb = (int64_t)bid * a.b.ntiles / a.nctas;
-  const int nt = (int)((int64_t)(bid + 1) * a.b.ntiles / a.nctas - tb);
-  const unsigned long long arrived = (unsigned long long)(a.nctas & 0xff);
-  if (tid == 0) s_abort = 0;
-  if (!stage_tiles<TIER>(a.b, tb, nt, raw, s32, s64, mbar, a.timeout_ns, a.err)) return;
-
-  for (int gen = 0; gen <= a.gens; ++gen) {
-    const int ring = gen % 3;
-    // the ring slot of generation gen+1 was last read before generation gen-1
-    // ended everywhere: CTA 0 clears it, and its fence orders the clear
-    // before its own contributions to this generation, which every reader
-    // acquires before contributing to generation gen+1
-    if (bid == 0 && tid < np) {
-      a.gacc[((gen + 1) % 3) * npad + tid] = 0ull;
+  for (int gen = 0; gen <= d.gens; ++gen, ++gg) {
+    unsigned long long* slot = ring + (gg % 3) * NP_MAX;
+    // the ring slot of the group's next generation was last read before the
+    // previous generation ended everywhere: rank 0 clears it, and its fence
+    // orders the clear before its own contributions to this generation, which
+    // every reader acquires before contributing to the next one
+    if (rank == 0 && tid < np) {
+      ring[((gg + 1) % 3) * NP_MAX + tid] = 0ull;
       __threadfence();
     }
     // trials u of this generation (the initial population at gen 0)
     if (gen == 0) {
-      if (tid < np) de_init(a.dc, tid, u + tid * D);
+      if (tid < np) de_init(d.dc, tid, sm.u + tid * D);
     } else {
       for (int t = tid; t < D * npad; t += blockDim.x) {
         const int j = t / npad, c = t - j * npad;
-        if (c < np) u[c * D + j] = de_component(a.dc, x, c, j, drp[c], drt[c]);
+        if (c < np) sm.u[c * D + j] = de_component(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c]);
       }
     }
-    if (tid < npad) acc[tid] = 0ull;
+    if (tid < npad) sm.acc[tid] = 0ull;
     __syncthreads();
-    prep_all<TIER>(u, np, npad, a.b, cdata, negA, kexp, SSE_BITS_DE);
-    eval_range<TIER, CGV>(a.b, tb, nt, s32, s64, cdata, negA, kexp, np, npad, anc, acc);
+    prep_all<TIER>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, SSE_BITS_DE);
+    if (resident) {
+      eval_range<TIER, CGV>(b, tb, nt, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, np, npad, sm.anc, sm.acc);
+    } else {
+      for (int c0 = 0; c0 < nt; c0 += a.sc_tiles) {
+        const int cn = min(a.sc_tiles, nt - c0);
+        if (!stage_tiles<TIER>(b, tb + c0, cn, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err)) return false;
+        eval_range<TIER, CGV>(b, tb + c0, cn, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, np, npad, sm.anc,
+                              sm.acc);
+      }
+    }
     if (tid < np) {
-      unsigned long long* w = &a.gacc[ring * npad + tid];
-      atomicAdd(w, (acc[tid] << 8) | 1ull);
+      unsigned long long* w = slot + tid;
+      atomicAdd(w, (sm.acc[tid] << 8) | 1ull);
       // wait for every CTA's contribution to this candidate, then select
       const uint64_t t_start = globaltimer_ns();
       unsigned long long v;
@@ -553,41 +573,88 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeArgs a) {
       while (((v = ld_acquire_u64(w)) & 0xffull) != arrived) {
         if ((++spins & 63) == 0) {
           if (ld_volatile_i32(a.err) != DEV_OK) {
-            s_abort = 1;
+            *s_abort = 1;
             break;
           }
           if (globaltimer_ns() - t_start > a.timeout_ns) {
             atomicExch(a.err, DEV_TIMEOUT);
-            s_abort = 1;
+            *s_abort = 1;
             break;
           }
         }
       }
-      const double f = fixed_to_double(v >> 8, kexp[tid]);
+      const double f = fixed_to_double(v >> 8, sm.kexp[tid]);
       // SSE values are non-negative: their bit patterns order like the values
-      if (gen == 0 || __double_as_longlong(f) <= __double_as_longlong(fx[tid])) {
-        fx[tid] = f;
+      if (gen == 0 || __double_as_longlong(f) <= __double_as_longlong(sm.fx[tid])) {
+        sm.fx[tid] = f;
 #pragma unroll
-        for (int j = 0; j < D; ++j) x[tid * D + j] = u[tid * D + j];
+        for (int j = 0; j < D; ++j) sm.x[tid * D + j] = sm.u[tid * D + j];
       }
-    } else if (gen < a.gens && tid >= NP_MAX && tid < NP_MAX + np) {
+    } else if (gen < d.gens && tid >= NP_MAX && tid < NP_MAX + np) {
       // the next generation's draws do not depend on selection: overlap them with the wait
       const int c = tid - NP_MAX;
-      de_draws(a.dc, np, c, (uint32_t)(gen + 1), &drp[c], &drt[c]);
+      de_draws(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c]);
     }
     __syncthreads();
-    if (s_abort) return;
+    if (*s_abort) return false;
   }
-  if (bid == 0) {
+  if (rank == 0) {
     if (tid == 0) {
       int best = 0;
       for (int i = 1; i < np; ++i)
-        if (__double_as_longlong(fx[i]) < __double_as_longlong(fx[best])) best = i;
-      for (int j = 0; j < D; ++j) a.out[j] = x[best * D + j];
-      a.out[D] = fx[best];
+        if (__double_as_longlong(sm.fx[i]) < __double_as_longlong(sm.fx[best])) best = i;
+      for (int j = 0; j < D; ++j) d.out[j] = sm.x[best * D + j];
+      d.out[D] = sm.fx[best];
     }
-    for (int i = tid; i < np * D; i += blockDim.x) a.pop_out[i] = x[i];
-    for (int i = tid; i < np; i += blockDim.x) a.fit_out[i] = fx[i];
+    if (d.pop_out)
+      for (int i = tid; i < np * D; i += blockDim.x) d.pop_out[i] = sm.x[i];
+    if (d.fit_out)
+      for (int i = tid; i < np; i += blockDim.x) d.fit_out[i] = sm.fx[i];
+  }
+  __syncthreads();
+  return true;
+}
+
+// Persistent DE launch over groups of blocks (one block: one group of all CTAs).
+// Launched cooperatively: the k CTAs of a group wait on one another.
+template <int TIER>
+__global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SmemLayout S = smem_layout(TIER, NP_MAX, a.sc_tiles, 16, a.esize_max, NP_MAX, NT);
+  DeSmem sm;
+  sm.mbar = reinterpret_cast<uint64_t*>(smem + S.off_mbar);
+  sm.x = reinterpret_cast<double*>(smem + S.off_pop);
+  sm.u = sm.x + NP_MAX * D;
+  sm.fx = sm.u + NP_MAX * D;
+  sm.cdata = smem + S.off_cdata;
+  sm.negA = reinterpret_cast<float*>(smem + S.off_negA);
+  sm.kexp = reinterpret_cast<int*>(smem + S.off_kexp);
+  sm.acc = reinterpret_cast<unsigned long long*>(smem + S.off_acc);
+  sm.drp = reinterpret_cast<uint32_t*>(smem + S.off_draw);
+  sm.drt = sm.drp + NP_MAX;
+  sm.anc = reinterpret_cast<uint4*>(smem + S.off_anc);
+  sm.s32 = reinterpret_cast<float*>(smem + S.off_samp);
+  sm.s64 = reinterpret_cast<double*>(smem + S.off_samp);
+  sm.raw = smem + S.off_raw;
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) s_abort = 0;
+  __syncthreads();
+
+  const int q = blockIdx.x / a.k, rank = blockIdx.x - q * a.k;
+  if (q >= a.ngroups) return;
+  unsigned long long* ring = a.ring + (size_t)q * 3 * NP_MAX;
+  unsigned long long gg = 0;
+  __shared__ DeBlockDesc s_desc;
+  for (int e = a.sched_off[q]; e < a.sched_off[q + 1]; ++e) {
+    // the block's descriptor lives in shared memory while it is solved
+    if (threadIdx.x == 0) s_desc = a.blocks[a.sched[e]];
+    __syncthreads();
+    const DeBlockDesc& d = s_desc;
+    bool ok;
+    if (TIER == TIER_F64 && d.cg == 16) ok = de_block<TIER, 16>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    else if (TIER == TIER_F64 && d.cg == 4) ok = de_block<TIER, 4>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    else ok = de_block<TIER, 8>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    if (!ok) return;
   }
 }
 

@@ -1,0 +1,78 @@
+"""GPU checks of the batched DE launch (many uneven blocks, one persistent
+launch under a CUDA graph): every block's fit is bit-identical to the same
+block solved alone, for every group size the launch may pick."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    build.build()
+    c = pt.Context(0)
+    yield c
+    c.close()
+
+
+def _mixed_blocks():
+    blocks = []
+    specs = [(3000, synth.I16, 17), (20_000, synth.I8, 40), (70_000, synth.I16, 64), (9_000, synth.F32, 128),
+             (41_000, synth.F16, 33), (257, synth.I16, 8), (120_000, synth.I16, 96), (5_000, synth.F64, 24)]
+    for i, (n, st, pop) in enumerate(specs):
+        b = synth.paper400k(100 + i, n=n, fs=5_000.0 + 1000 * i, storage=st, pop=pop, gens=25)
+        b.block_id = i
+        b.de_seed = 7 + i
+        blocks.append(b)
+    return blocks
+
+
+def test_batch_bit_identical_to_single_solves(ctx):
+    import paper_1906_10598_b300 as pt
+    blocks = _mixed_blocks()
+    alone = []
+    for b in blocks:
+        ctx.load_block(b.samples, b.fs, b.t0, b.scale)
+        alone.append(ctx.de_solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, pt.TIER_F64, block_id=b.block_id))
+    for k in (0, 1, 3, 8):
+        batch = pt.Batch(ctx, blocks, pt.TIER_F64, group_ctas=k)
+        batch.run()
+        params, sse = batch.results()
+        for i, (p1, s1) in enumerate(alone):
+            assert np.array_equal(params[i], p1), (k, i)
+            assert sse[i] == s1, (k, i)
+        info = batch.info()
+        assert info["nblocks"] == len(blocks) and info["group_ctas"] >= 1
+        # a second run of the same batch (graph replay) gives the same fits
+        batch.run()
+        p2, s2 = batch.results()
+        assert np.array_equal(p2, params) and np.array_equal(s2, sse)
+        batch.close()
+
+
+def test_batch_fits_match_oracle_objective(ctx):
+    import paper_1906_10598_b300 as pt
+    blocks = synth.batch(3, nblocks=6, n_lo=20_000, n_hi=80_000, evals=6_000)
+    batch = pt.Batch(ctx, blocks, pt.TIER_F64)
+    batch.run()
+    params, sse = batch.results()
+    info = batch.info()
+    assert info["predicted_ms"] > 0 and info["tune_rate"] > 0
+    for i, b in enumerate(blocks):
+        want = oracle.sse(b.values(), b.fs, b.t0, params[i])
+        assert sse[i] == pytest.approx(want, rel=1e-6)
+        assert np.all(params[i] >= b.bounds[:, 0] - 1e-12) and np.all(params[i] <= b.bounds[:, 1] + 1e-12)
+    batch.close()
+
+
+def test_batch_invalid(ctx):
+    import paper_1906_10598_b300 as pt
+    b = synth.paper400k(1, n=1000, gens=3)
+    b.pop = 3
+    with pytest.raises(pt.PhaseTrackError):
+        pt.Batch(ctx, [b])
