@@ -248,6 +248,96 @@ def run_gpu(args):
     return 0
 
 
+def run_batch(args):
+    """256 independent blocks of uneven length (N log-uniform 50K-1M int16, fs 1-50
+    kHz, pop 32-128, G = ceil(80000/pop)) in one persistent launch under a CUDA
+    graph, launch shape chosen by the autotuner. Compared with the all-FP64
+    single-block form on a sample of the same blocks."""
+    import torch
+    import oracle
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    build.build()
+    blocks = synth.batch(0, nblocks=args.nblocks)
+    ctx = pt.Context(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx.set_stream(stream.cuda_stream)
+    t = time.perf_counter()
+    batch = pt.Batch(ctx, blocks, pt.TIER_F64)
+    create_s = time.perf_counter() - t
+    info = batch.info()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        batch.run()
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ms.append(batch.run())
+    clocks = sampler.stop()
+    params, sse = batch.results()
+    mean_s = float(np.mean(ms)) * 1e-3
+    evals = info["sample_evals"]
+    # fit check on a few blocks against the oracle objective
+    rel = []
+    for i in range(0, len(blocks), max(1, len(blocks) // 4)):
+        b = blocks[i]
+        want = oracle.sse(b.values(), b.fs, b.t0, params[i])
+        rel.append(abs(sse[i] - want) / want)
+    # all-FP64 single-block form on a sample of the blocks (one pt_de_solve each)
+    order = np.argsort([b.n for b in blocks])
+    sample_ids = [int(order[len(order) // 4]), int(order[len(order) // 2])]
+    plain_s, plain_evals, fast_s = 0.0, 0.0, 0.0
+    for i in sample_ids:
+        b = blocks[i]
+        ctx.load_block(b.samples, b.fs, b.t0, b.scale)
+        ctx.de_solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, pt.TIER_PLAIN, block_id=b.block_id)
+        plain_s += ctx.last_kernel_ms() * 1e-3
+        ctx.de_solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, pt.TIER_F64, block_id=b.block_id)
+        fast_s += ctx.last_kernel_ms() * 1e-3
+        plain_evals += b.sample_evals()
+    plain_rate = plain_evals / plain_s
+    # end to end: fresh batch every step (H2D of every block's samples, launch, results)
+    e2e = []
+    for _ in range(max(1, args.steps // 3)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        bb = pt.Batch(ctx, blocks, pt.TIER_F64)
+        bb.run()
+        bb.results()
+        bb.close()
+        e2e.append(time.perf_counter() - t)
+    nbytes = int(sum(b.samples.nbytes for b in blocks))
+    line = {"metric": "batched objective sample-evals/s", "value": evals / mean_s, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch{len(blocks)}_int16_n50k-1m_pop32-128", "blocks": len(blocks),
+                       "total_samples": int(sum(b.n for b in blocks)), "l2": "flushed between steps",
+                       "group_ctas": info["group_ctas"], "groups": info["ngroups"],
+                       "uses_graph": info["uses_graph"], "autotune_predicted_ms": info["predicted_ms"],
+                       "tune_rate_per_cta": info["tune_rate"], "tune_gen_us": info["tune_gen_us"],
+                       "tune_sync_us": info["tune_sync_us"], "create_s": create_s},
+            "blocks_per_s": len(blocks) / mean_s,
+            "roofline": {"bound": "alu", "achieved": evals / mean_s, "peak": SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6,
+                         "unit": UNIT, "frac": evals / mean_s / (SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6),
+                         "traffic": None, "kernel": "k_de<TIER_F64> (grouped)"},
+            "plain_f64_single_block": {"sample_evals_per_s": plain_rate,
+                                       "blocks_per_s_est": len(blocks) / (evals / plain_rate),
+                                       "sampled_blocks": sample_ids,
+                                       "default_tier_single_block_s": fast_s, "plain_tier_single_block_s": plain_s},
+            "fit_sse_rel_err_vs_oracle_max": float(max(rel)),
+            "clocks": clocks, "gpu_launches": args.steps,
+            "e2e": {"value": evals / float(np.mean(e2e)), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": len(blocks) * 48}}
+    print(json.dumps(line))
+    batch.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,9 +345,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--mode", default="single", choices=["single", "batch"],
+                    help="single: the 400K-block fit (default); batch: 256 uneven blocks in one launch")
+    ap.add_argument("--nblocks", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

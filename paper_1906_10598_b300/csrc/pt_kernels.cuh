@@ -537,7 +537,8 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     // previous generation ended everywhere: rank 0 clears it, and its fence
     // orders the clear before its own contributions to this generation, which
     // every reader acquires before contributing to the next one
-    if (rank == 0 && tid < np) {
+    // (every word of the slot: the group's next block may have a larger population)
+    if (rank == 0 && tid < NP_MAX) {
       ring[((gg + 1) % 3) * NP_MAX + tid] = 0ull;
       __threadfence();
     }
@@ -565,7 +566,14 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     }
     if (tid < np) {
       unsigned long long* w = slot + tid;
-      atomicAdd(w, (sm.acc[tid] << 8) | 1ull);
+      const unsigned long long contrib = (sm.acc[tid] << 8) | 1ull;
+      if (rank == 0) {
+        // release: orders rank 0's clear of the next slot (by any of its
+        // threads, before the CTA barrier above) before this contribution
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(w), "l"(contrib) : "memory");
+      } else {
+        atomicAdd(w, contrib);
+      }
       // wait for every CTA's contribution to this candidate, then select
       const uint64_t t_start = globaltimer_ns();
       unsigned long long v;
