@@ -211,6 +211,42 @@ PT_API int pt_batch_get_info(const pt_batch* batch, pt_batch_info* info);
 /* Release the batch's device memory and graph. NULL is allowed. */
 PT_API void pt_batch_destroy(pt_batch* batch);
 
+/* ---- Objective without allocation ------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for host
+ * programs that must not allocate device memory on their call path, such as
+ * a real-time recording pipeline that reserves the GPU's memory up front in
+ * its own pool, or a framework that forbids driver allocations after
+ * start-up. It computes what pt_objective computes without a context and
+ * without calling cudaMalloc, cudaFree or any allocating routine:
+ *   - every input and output is a device buffer the caller owns;
+ *   - the only scratch is a fixed array in the library's device memory
+ *     (PT_NOALLOC_MAX_CANDIDATES + 32 64-bit words, about 33 KB), which every
+ *     GPU that loads the library holds until the process exits.
+ * Arguments:
+ *   samples   device pointer to ceil(n/256)*256 readable values of type dtype
+ *             (values past n are read and ignored).
+ *   n, dtype, scale, fs, t0  as in pt_load_block.
+ *   smax      an upper bound on |scale * sample|; 0 takes the type's range
+ *             (128, 32768, 65504 times scale for I8, I16, F16). F32 and F64
+ *             samples need an explicit bound.
+ *   cands     device pointer, ncand rows of 5 doubles (A, phi0, f0, f1, f2).
+ *   ncand     1 <= ncand <= PT_NOALLOC_MAX_CANDIDATES; larger is PT_EINVAL.
+ *   sse_out   device pointer, ncand doubles.
+ *   tier      PT_TIER_*.
+ *   stream    cudaStream_t to launch on (NULL: the legacy default stream).
+ * The call is synchronous on `stream`. The first call on a device looks up
+ * the scratch array's device address with that device current and caches it;
+ * make that first call before any stream capture. Every call clears the
+ * scratch before use (the array keeps the previous call's contents); calls
+ * whose work overlaps on the GPU share the one array and race, so callers must
+ * serialise them (one stream, or one call at a time per device).
+ * Errors: PT_EINVAL (sizes, pointers that are not device memory, a missing
+ * bound), PT_ECUDA, PT_ETIMEOUT. */
+#define PT_NOALLOC_MAX_CANDIDATES 4096
+PT_API int pt_objective_noalloc(const void* samples, int64_t n, int dtype, double scale, double fs, double t0,
+                                double smax, const double* cands, int64_t ncand, double* sse_out, int tier,
+                                void* stream);
+
 /* Device time in milliseconds of the last pt_objective / pt_de_solve kernel
  * work, measured with CUDA events on the context's stream. */
 PT_API int pt_last_kernel_ms(const pt_ctx* ctx, float* ms);

@@ -415,7 +415,7 @@ __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, 
 
 // ---------------------------------------------------------------------------
 
-__global__ void k_absmax(const void* samples, int64_t n, int dtype, unsigned long long* out) {
+static __global__ void k_absmax(const void* samples, int64_t n, int dtype, unsigned long long* out) {
   double m = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     m = fmax(m, fabs(load_physical(samples, dtype, i, 1.0)));
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   if (tid < nc) atomicAdd(&a.acc[cb + tid], acc[tid]);
 }
 
-__global__ void k_finalize(const double* cands, int ncand, const unsigned long long* acc, int64_t n, float smax_f,
+static __global__ void k_finalize(const double* cands, int ncand, const unsigned long long* acc, int64_t n, float smax_f,
                            double* sse) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncand) return;

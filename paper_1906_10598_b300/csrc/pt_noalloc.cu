@@ -1,0 +1,169 @@
+// pt_objective_noalloc: the objective of Eq. 2-2-4 for callers that cannot
+// allocate device memory.
+//
+// Some host programs may not allocate GPU memory once they are running, for
+// example a station's real-time recording pipeline that reserves the device's
+// memory up front in its own pool, or a host framework that forbids driver
+// allocations after start-up so its memory use stays fixed. They cannot create
+// a pt_ctx (which allocates its buffers) or call pt_objective (which grows
+// its scratch on demand). This entry point needs no context: the caller passes
+// device buffers for every input and output, and the only scratch is a
+// file-scope device array of fixed size that every GPU loading the library
+// holds until the process exits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "../../include/phasetrack.h"
+#include "pt_kernels.cuh"
+
+namespace {
+
+using namespace pt;
+
+constexpr int NOALLOC_MAX_CANDS = PT_NOALLOC_MAX_CANDIDATES;
+
+// Accumulators of up to NOALLOC_MAX_CANDS candidates, then the error word.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[NOALLOC_MAX_CANDS + 32];
+
+std::mutex g_mu;
+constexpr int MAX_DEVICES = 64;
+unsigned long long* g_scratch_addr[MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device. In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with that device current, and cached.
+int scratch_address(int dev, unsigned long long** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (dev < 0 || dev >= MAX_DEVICES) return PT_EINVAL;
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return PT_ECUDA;
+    }
+    g_scratch_addr[dev] = static_cast<unsigned long long*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return PT_OK;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <int TIER, int CGV>
+int launch(const BlockArgs& b, const double* cands, int ncand, unsigned long long* acc, int* err, cudaStream_t s,
+           int sms, size_t optin) {
+  ObjArgs a{};
+  a.b = b;
+  a.cands = cands;
+  a.ncand = ncand;
+  a.cpc = std::min(((ncand + CGV - 1) / CGV) * CGV, NP_MAX);
+  const int ny = (ncand + a.cpc - 1) / a.cpc;
+  const int64_t want = 2LL * sms;
+  a.tpc = (int)std::max<int64_t>(1, std::min<int64_t>((b.ntiles * ny + want - 1) / want, 32));
+  const int nx = (int)((b.ntiles + a.tpc - 1) / a.tpc);
+  a.acc = acc;
+  a.err = err;
+  a.timeout_ns = 2000000000ull;
+  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, b.esize, 0, NT);
+  if (S.total > optin) return PT_EINVAL;
+  if (cudaFuncSetAttribute(k_objective<TIER, CGV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total) !=
+      cudaSuccess)
+    return PT_ECUDA;
+  k_objective<TIER, CGV><<<dim3(nx, ny), NT, S.total, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ECUDA;
+}
+
+int launch_any(int tier, const BlockArgs& b, const double* cands, int ncand, unsigned long long* acc, int* err,
+               cudaStream_t s, int sms, size_t optin) {
+  if (tier == PT_TIER_PLAIN) return launch<TIER_PLAIN, 8>(b, cands, ncand, acc, err, s, sms, optin);
+  if (tier == PT_TIER_DF32) return launch<TIER_DF32, 8>(b, cands, ncand, acc, err, s, sms, optin);
+  if (tier == PT_TIER_F32) return launch<TIER_F32, 8>(b, cands, ncand, acc, err, s, sms, optin);
+  const int n = std::min(ncand, NP_MAX);
+  // same item width rule as pt_objective: the width in {16, 8, 4} padding n least
+  int cg = 16, pad = (n + 15) / 16 * 16;
+  if ((n + 7) / 8 * 8 < pad) {
+    cg = 8;
+    pad = (n + 7) / 8 * 8;
+  }
+  if ((n + 3) / 4 * 4 < pad) cg = 4;
+  if (cg == 16) return launch<TIER_F64, 16>(b, cands, ncand, acc, err, s, sms, optin);
+  if (cg == 8) return launch<TIER_F64, 8>(b, cands, ncand, acc, err, s, sms, optin);
+  return launch<TIER_F64, 4>(b, cands, ncand, acc, err, s, sms, optin);
+}
+
+}  // namespace
+
+extern "C" int pt_objective_noalloc(const void* samples, int64_t n, int dtype, double scale, double fs, double t0,
+                                    double smax, const double* cands, int64_t ncand, double* sse_out, int tier,
+                                    void* stream) {
+  int esize = 0;
+  double bound = 0.0;
+  switch (dtype) {
+    case PT_I8: esize = 1; bound = 128.0; break;
+    case PT_I16: esize = 2; bound = 32768.0; break;
+    case PT_F16: esize = 2; bound = 65504.0; break;
+    case PT_F32: esize = 4; break;
+    case PT_F64: esize = 8; break;
+    default: return PT_EINVAL;
+  }
+  if (n < 1 || n > ((int64_t)1 << 36) || ncand < 1 || ncand > NOALLOC_MAX_CANDS || !(scale > 0.0) ||
+      !std::isfinite(scale) || !(fs > 0.0) || !std::isfinite(fs) || !std::isfinite(t0) || tier < PT_TIER_F64 ||
+      tier > PT_TIER_F32)
+    return PT_EINVAL;
+  if (!(smax > 0.0)) {
+    if (bound == 0.0) return PT_EINVAL;  // float samples: the caller must bound them
+    smax = bound * scale;
+  }
+  if (!std::isfinite(smax)) return PT_EINVAL;
+  if (!on_device(samples) || !on_device(cands) || !on_device(sse_out)) return PT_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PT_ECUDA;
+  unsigned long long* scratch = nullptr;
+  int rc = scratch_address(dev, &scratch);
+  if (rc != PT_OK) return rc;
+  int sms = 0, optin = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return PT_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* acc = scratch;
+  int* err = reinterpret_cast<int*>(scratch + NOALLOC_MAX_CANDS);
+  BlockArgs b{};
+  b.samples = samples;
+  b.n = n;
+  b.ntiles = (n + L - 1) / L;
+  b.dtype = dtype;
+  b.esize = esize;
+  b.scale = scale;
+  b.smax = smax;
+  b.smax_f = (float)smax;
+  b.t0 = t0;
+  b.h = 1.0 / fs;
+  b.t0sq_2 = t0 * t0 / 2.0;
+  b.t0cu_6 = t0 * t0 * t0 / 6.0;
+  b.h2_2 = b.h * b.h / 2.0;
+  b.h3_6 = b.h * b.h * b.h / 6.0;
+  // the array keeps the previous call's contents: clear the accumulators and
+  // the error word before every call
+  if (cudaMemsetAsync(scratch, 0, (NOALLOC_MAX_CANDS + 1) * sizeof(unsigned long long), s) != cudaSuccess)
+    return PT_ECUDA;
+  if ((rc = launch_any(tier, b, cands, (int)ncand, acc, err, s, sms, (size_t)optin)) != PT_OK) return rc;
+  k_finalize<<<(int)((ncand + 255) / 256), 256, 0, s>>>(cands, (int)ncand, acc, n, (float)smax, sse_out);
+  if (cudaGetLastError() != cudaSuccess) return PT_ECUDA;
+  int h_err = 0;
+  if (cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return PT_ECUDA;
+  if (h_err == DEV_TIMEOUT) return PT_ETIMEOUT;
+  return h_err == DEV_OK ? PT_OK : PT_ECUDA;
+}
