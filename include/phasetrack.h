@@ -211,6 +211,76 @@ PT_API int pt_batch_get_info(const pt_batch* batch, pt_batch_info* info);
 /* Release the batch's device memory and graph. NULL is allowed. */
 PT_API void pt_batch_destroy(pt_batch* batch);
 
+/* ---- Serving: station streams, continuous batching -------------------------
+ * Blocks arrive from several station streams as they fill (Sec. 3.1.4: the
+ * software processes the data stream block by block without manual
+ * intervention). pt_submit queues a block and returns at once; a worker
+ * thread of the context admits queued blocks into device slots as slots and
+ * device memory free up, each admitted block running on its own CUDA stream
+ * so its work overlaps the others already on the device; pt_poll collects a
+ * finished fit. A block's fit is bit-identical to pt_de_solve_ex on the same
+ * block alone, whatever else is in flight. */
+
+typedef struct pt_request {
+  pt_block_spec block; /* samples are copied by pt_submit */
+  int tier;
+  int stream_id;       /* caller's station-stream id, returned in the result */
+} pt_request;
+
+typedef struct pt_result {
+  pt_fit fit;
+  int status;          /* PT_OK, or the error the fit ended with */
+  int stream_id;
+  double t_submit;     /* seconds on the library's monotonic clock (pt_clock) */
+  double t_admit;      /* when the block started on the device */
+  double t_done;       /* when the worker saw the fit complete */
+} pt_result;
+
+/* Configure the serving loop (before the first pt_submit; later calls fail
+ * with PT_EINVAL while requests are in flight):
+ *   max_inflight      blocks on the device at once (1..32)
+ *   ctas_per_request  CTAs of each block's cooperative launch; 0 = SMs / max_inflight
+ *   mem_budget_bytes  device memory the slots may hold; 0 = half of the free memory
+ *   max_queued        blocks waiting for a slot before pt_submit returns PT_EAGAIN */
+PT_API int pt_serve_configure(pt_ctx* ctx, int max_inflight, int ctas_per_request, int64_t mem_budget_bytes,
+                              int max_queued);
+
+/* Queue one block. Returns PT_OK and a ticket, PT_EAGAIN when the queue is
+ * full (retry after pt_poll has collected results), or PT_EINVAL (bad
+ * arguments, or a block larger than the memory budget). Non-blocking. */
+PT_API int pt_submit(pt_ctx* ctx, const pt_request* req, uint64_t* ticket);
+
+/* PT_OK and the result (which is then released), PT_PENDING while queued or
+ * running, PT_EINVAL for an unknown ticket. Non-blocking. */
+PT_API int pt_poll(pt_ctx* ctx, uint64_t ticket, pt_result* out);
+
+/* Seconds on the monotonic clock used by pt_result. */
+PT_API double pt_clock(void);
+
+/* ---- Block-to-block tracking helpers (host only) ---------------------------
+ * Running-time range setting of Sec. 3.1.1: the ranges for block n+1 are
+ * extrapolated from block n's fit. prev is (A, phi0, f0, f1, f2) of block n
+ * about its centre; dt is the time from block n's centre to block n+1's
+ * centre; T_next the length of block n+1. Output bounds (5 x 2):
+ *   A     +-10 % of A;
+ *   phi0  the full circle [-pi, pi);
+ *   f0    the instantaneous frequency (Eq. 3-1-1) between the shared border
+ *         and the far end of block n+1, widened by min_f0 on each side;
+ *   f1    the frequency rate over the same span, widened by min_f1;
+ *   f2    f2 +- min_f2 (the paper narrows c3 after the first fit).
+ * min_* <= 0 take 2/T_next, 4/T_next^2, 24/T_next^3. */
+PT_API int pt_warm_bounds(const double prev[5], double dt, double T_next, double min_f0, double min_f1,
+                          double min_f2, double bounds_out[10]);
+
+/* Continuity check of Eq. 3-1-2: the phase (mod 2 pi) and frequency of block
+ * a (length Ta, about its centre) at its right border against block b
+ * (length Tb, about its own centre) at its left border; the two borders are
+ * the same instant for contiguous blocks.
+ * Writes |dphi| (rad, wrapped to [0, pi]) and |dF| (rad/s); returns 1 if both
+ * are within the thresholds, 0 if not, PT_EINVAL for bad arguments. */
+PT_API int pt_continuity(const double a[5], double Ta, const double b[5], double Tb, double max_dphi,
+                         double max_dfreq, double* dphi, double* dfreq);
+
 /* ---- Objective without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for host
  * programs that must not allocate device memory on their call path, such as

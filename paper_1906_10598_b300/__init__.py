@@ -291,3 +291,119 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---- serving and block-to-block tracking -----------------------------------------
+
+
+class Request(ctypes.Structure):
+    """Mirror of ``pt_request``."""
+    _fields_ = [("block", BlockSpec), ("tier", ctypes.c_int), ("stream_id", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    """Mirror of ``pt_result``."""
+    _fields_ = [("fit", Fit), ("status", ctypes.c_int), ("stream_id", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+def _serve_protos(lib):
+    if getattr(lib, "_serve_protos", False):
+        return
+    vp = ctypes.c_void_p
+    lib.pt_serve_configure.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int]
+    lib.pt_serve_configure.restype = ctypes.c_int
+    lib.pt_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.pt_submit.restype = ctypes.c_int
+    lib.pt_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+    lib.pt_poll.restype = ctypes.c_int
+    lib.pt_clock.argtypes = []
+    lib.pt_clock.restype = ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.pt_warm_bounds.argtypes = [dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, dp]
+    lib.pt_warm_bounds.restype = ctypes.c_int
+    lib.pt_continuity.argtypes = [dp, ctypes.c_double, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+    lib.pt_continuity.restype = ctypes.c_int
+    lib._serve_protos = True
+
+
+def _dvec(a, n):
+    v = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    assert v.size == n
+    return v
+
+
+def warm_bounds(prev, dt: float, T_next: float, min_f0: float = 0.0, min_f1: float = 0.0, min_f2: float = 0.0):
+    """pt_warm_bounds: running-time ranges of the next block from the previous fit (5 x 2)."""
+    lib = load_library()
+    _serve_protos(lib)
+    p = _dvec(prev, 5)
+    out = np.zeros(10, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib.pt_warm_bounds(p.ctypes.data_as(dp), float(dt), float(T_next), float(min_f0), float(min_f1),
+                            float(min_f2), out.ctypes.data_as(dp))
+    if rc != PT_OK:
+        raise PhaseTrackError(rc, "pt_warm_bounds")
+    return out.reshape(5, 2)
+
+
+def continuity(a, Ta: float, b, Tb: float, max_dphi: float, max_dfreq: float):
+    """pt_continuity: (passed, |dphi| rad, |dF| rad/s) at the shared border of two blocks."""
+    lib = load_library()
+    _serve_protos(lib)
+    av, bv = _dvec(a, 5), _dvec(b, 5)
+    dphi, dfreq = ctypes.c_double(), ctypes.c_double()
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib.pt_continuity(av.ctypes.data_as(dp), float(Ta), bv.ctypes.data_as(dp), float(Tb), float(max_dphi),
+                           float(max_dfreq), ctypes.byref(dphi), ctypes.byref(dfreq))
+    if rc < 0:
+        raise PhaseTrackError(rc, "pt_continuity")
+    return bool(rc), dphi.value, dfreq.value
+
+
+class Server:
+    """The context's serving loop: ``submit`` queues a block (returns a ticket,
+    or None when the queue is full), ``poll`` returns a result dict or None."""
+
+    def __init__(self, ctx: Context, max_inflight: int = 4, ctas_per_request: int = 0, mem_budget_bytes: int = 0,
+                 max_queued: int = 64):
+        self._ctx = ctx
+        self._lib = ctx._lib
+        _serve_protos(self._lib)
+        ctx._check(self._lib.pt_serve_configure(ctx.handle, int(max_inflight), int(ctas_per_request),
+                                                int(mem_budget_bytes), int(max_queued)))
+
+    def submit(self, block, tier: int = TIER_F64, stream_id: int = 0, bounds=None):
+        s = np.ascontiguousarray(block.samples)
+        r = Request()
+        sp = r.block
+        sp.samples = s.ctypes.data
+        sp.n = s.size
+        sp.dtype = _NP_TO_PT[s.dtype]
+        sp.scale, sp.fs, sp.t0 = float(block.scale), float(block.fs), float(block.t0)
+        bb = np.asarray(block.bounds if bounds is None else bounds, dtype=np.float64).reshape(-1)
+        for j in range(10):
+            sp.bounds[j] = float(bb[j])
+        sp.pop, sp.gens = int(block.pop), int(block.gens)
+        sp.F, sp.CR = float(block.F), float(block.CR)
+        sp.seed, sp.block_id = int(block.de_seed), int(block.block_id)
+        r.tier, r.stream_id = int(tier), int(stream_id)
+        t = ctypes.c_uint64()
+        rc = self._lib.pt_submit(self._ctx.handle, ctypes.byref(r), ctypes.byref(t))
+        if rc == PT_EAGAIN:
+            return None
+        self._ctx._check(rc)
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        r = Result()
+        rc = self._lib.pt_poll(self._ctx.handle, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if rc == PT_PENDING:
+            return None
+        self._ctx._check(rc)
+        return {"params": np.array(list(r.fit.params)), "sse": r.fit.sse, "status": r.status,
+                "stream_id": r.stream_id, "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done}
+
+    def clock(self) -> float:
+        return float(self._lib.pt_clock())
