@@ -434,6 +434,63 @@ def run_serve(args):
     return 0
 
 
+def run_precision(args):
+    """Precision sweep on the 400K block: samples stored as int8 / FP16 / FP32,
+    phase evaluated by the FP64-anchored default tier, the double-float FP32
+    tier and the naive FP32 tier. Per (storage, tier) over `--seeds` seeds:
+    the objective's relative error against the oracle's SSE at the same
+    parameters, and the fitted phi0/f0/f1/f2 errors against the oracle's own
+    fits (tests/golden/precision_oracle_fits.json, written by the oracle alone)."""
+    import oracle
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    build.build()
+    ref_path = os.path.join(ROOT, "tests", "golden", "precision_oracle_fits.json")
+    ref = json.load(open(ref_path)) if os.path.exists(ref_path) else {}
+    ctx = pt.Context(0)
+    tiers = {"f64-anchored": pt.TIER_F64, "double-float": pt.TIER_DF32, "naive-f32": pt.TIER_F32}
+    rows = {}
+    for st in ("i8", "f16", "f32"):
+        for seed in range(args.seeds):
+            b = synth.precision(seed, synth.STORAGE_NAMES[st])
+            ctx.load_block(b.samples, b.fs, b.t0, b.scale)
+            vals = b.values()
+            r = ref.get(f"{st}/{seed}")
+            for name, tier in tiers.items():
+                p, f = ctx.de_solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, tier)
+                ms = ctx.last_kernel_ms()
+                want = oracle.sse(vals, b.fs, b.t0, p)
+                d = rows.setdefault((st, name), {"sse_rel": [], "ms": [], "dphi0": [], "df0": [], "df1": [],
+                                                 "df2": [], "truth_df0": [], "n_ref": 0})
+                d["sse_rel"].append(abs(f - want) / want)
+                d["ms"].append(ms)
+                d["truth_df0"].append(abs(p[2] - b.truth[2]))
+                if r is not None:
+                    q = np.array(r["params"])
+                    d["dphi0"].append(abs(float(np.angle(np.exp(1j * (p[1] - q[1]))))))
+                    d["df0"].append(abs(p[2] - q[2]))
+                    d["df1"].append(abs(p[3] - q[3]))
+                    d["df2"].append(abs(p[4] - q[4]))
+                    d["n_ref"] += 1
+    table = []
+    for (st, name), d in rows.items():
+        e = {"storage": st, "tier": name, "seeds": len(d["sse_rel"]), "oracle_fits": d["n_ref"],
+             "sse_rel_err_max": float(np.max(d["sse_rel"])), "sse_rel_err_median": float(np.median(d["sse_rel"])),
+             "fit_ms_median": float(np.median(d["ms"])),
+             "f0_err_vs_truth_hz_median": float(np.median(d["truth_df0"]))}
+        for k in ("dphi0", "df0", "df1", "df2"):
+            if d[k]:
+                e[k + "_vs_oracle_median"] = float(np.median(d[k]))
+                e[k + "_vs_oracle_max"] = float(np.max(d[k]))
+        if d["dphi0"]:
+            e["within_1e-3rad_1e-5Hz"] = float(np.mean([(a <= 1e-3 and c <= 1e-5) for a, c in
+                                                        zip(d["dphi0"], d["df0"])]))
+        table.append(e)
+    print(json.dumps({"metric": "precision sweep", "workload": "paper400k x storage x tier", "rows": table}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,13 +498,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "precision"],
                     help="single: the 400K-block fit (default); batch: 256 uneven blocks in one launch; "
                          "serve: 4 station streams through pt_submit/pt_poll")
     ap.add_argument("--nblocks", type=int, default=256)
     ap.add_argument("--speedup", type=float, default=20.0, help="serve: real-time compression factor")
     ap.add_argument("--sim-seconds", type=float, default=120.0, help="serve: simulated stream duration")
     ap.add_argument("--inflight", type=int, default=4, help="serve: blocks on the device at once")
+    ap.add_argument("--seeds", type=int, default=32, help="precision: seeds per storage")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -455,6 +513,8 @@ def main():
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "precision":
+        return run_precision(args)
     return run_gpu(args)
 
 
