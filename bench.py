@@ -159,7 +159,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    blk = synth.paper400k(rank)
+    blk = synth.paper400k(rank, gens=args.gens)
     ctx = pt.Context(local)
     # a dedicated stream: the library launches on it and the CUDA events below
     # are recorded on it, so they bracket exactly the library's work
@@ -506,6 +506,8 @@ def main():
     ap.add_argument("--sim-seconds", type=float, default=120.0, help="serve: simulated stream duration")
     ap.add_argument("--inflight", type=int, default=4, help="serve: blocks on the device at once")
     ap.add_argument("--seeds", type=int, default=32, help="precision: seeds per storage")
+    ap.add_argument("--gens", type=int, default=1250,
+                    help="single: DE generations (the workload is 1250; smaller only for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
