@@ -187,11 +187,23 @@ __device__ __forceinline__ double de_component(const DeControls& dc, const doubl
   double v = __dadd_rn(x[r0 * D + j], __dmul_rn(dc.F, __dsub_rn(x[r1 * D + j], x[r2 * D + j])));
   if (j == 1 && dc.periodic) {
     const double d = __dsub_rn(v, dc.lo[j]);
-    // floor(d / 2pi) is 0 without dividing when 0 <= d is safely below 2pi
-    if (dkey(d) < 0 || dkey(d) >= dkey(TWO_PI * (1.0 - 0x1p-50))) {
-      const double k = floor(__ddiv_rn(d, TWO_PI));
-      v = __dsub_rn(v, __dmul_rn(k, TWO_PI));
+    // k = floor(fl(d / 2pi)) without dividing: for d in [-4pi, 5pi) the
+    // quotient crosses -1, 0, 1, 2 exactly where d crosses the exact doubles
+    // -2pi, 0, 2pi, 4pi (the quotient's rounding threshold lies within half
+    // an ulp of d of each), so comparing d with them gives the same k as the
+    // rounded division; outside that range, divide.
+    const long long kd = dkey(d);
+    double k;
+    if (kd >= dkey(-2.0 * TWO_PI) && kd < dkey(2.5 * TWO_PI)) {
+      k = kd >= dkey(2.0 * TWO_PI) ? 2.0
+          : kd >= dkey(TWO_PI)     ? 1.0
+          : kd >= dkey(0.0)        ? 0.0
+          : kd >= dkey(-TWO_PI)    ? -1.0
+                                   : -2.0;
+    } else {
+      k = floor(__ddiv_rn(d, TWO_PI));
     }
+    if (k != 0.0) v = __dsub_rn(v, __dmul_rn(k, TWO_PI));
   } else if (dkey(v) < dkey(dc.lo[j])) {
     v = __dmul_rn(__dadd_rn(dc.lo[j], parent), 0.5);
   } else if (dkey(v) > dkey(dc.hi[j])) {
