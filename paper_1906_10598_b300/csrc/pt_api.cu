@@ -15,6 +15,9 @@
 #include "pt_internal.h"
 #include "pt_kernels.cuh"
 
+static_assert(pt::HOST_NP_MAX == pt::NP_MAX && pt::HOST_RING_STRIDE == pt::RING_STRIDE && pt::HOST_L == pt::L,
+              "host mirrors of the device constants");
+
 namespace pt {
 
 bool is_device_ptr(const void* p) {
@@ -271,7 +274,7 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   a.err = d_err;
   a.timeout_ns = c->timeout_ns;
   if (!(mode & DE_LAUNCH)) return PT_OK;
-  PT_CUDA(c, cudaMemsetAsync(ring, 0, (size_t)ngroups * 3 * NP_MAX * sizeof(unsigned long long), s));
+  PT_CUDA(c, cudaMemsetAsync(ring, 0, (size_t)ngroups * RING_GROUP_WORDS * sizeof(unsigned long long), s));
   PT_CUDA(c, cudaMemsetAsync(d_err, 0, sizeof(int), s));
   switch (tier) {
     case PT_TIER_F64: return launch_de_t<TIER_F64>(c, s, a);
@@ -328,7 +331,7 @@ int pt_create(pt_ctx** out, int device) {
   c->smem_optin = prop.sharedMemPerBlockOptin;
   if (bad(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking))) return PT_ECUDA;
   c->stream = c->own_stream;
-  if (bad(cudaMalloc(&c->d_ring, (size_t)c->sms * 3 * NP_MAX * sizeof(unsigned long long)))) return PT_ENOMEM;
+  if (bad(cudaMalloc(&c->d_ring, (size_t)c->sms * RING_GROUP_WORDS * sizeof(unsigned long long)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_err, sizeof(int)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_out, 8 * sizeof(double)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_pop, PT_POP_MAX * D * sizeof(double)))) return PT_ENOMEM;

@@ -263,7 +263,7 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
   }
   b->predicted_ms = best * 1e3;
   if ((e = cudaMalloc(&b->d_desc, de_desc_bytes(nblocks, b->ngroups))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_ring, (size_t)b->ngroups * 3 * HOST_NP_MAX * sizeof(unsigned long long))) !=
+      (e = cudaMalloc(&b->d_ring, (size_t)b->ngroups * RING_GROUP_WORDS * sizeof(unsigned long long))) !=
           cudaSuccess)
     return bail(fail(c, PT_ENOMEM, "pt_batch_create: descriptor allocation failed"));
   if ((rc = launch_de_groups(c, s, tier, b->blocks.data(), nblocks, b->sched.data(), b->off.data(), b->ngroups,

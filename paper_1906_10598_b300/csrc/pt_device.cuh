@@ -27,6 +27,9 @@ constexpr int D = 5;             // (A, phi0, f0, f1, f2)
 constexpr int M = 8;             // samples per lane per tile
 constexpr int L = 32 * M;        // samples per tile
 constexpr int NP_MAX = 128;      // largest population / candidate batch per CTA
+// Each candidate's word of the DE exchange ring sits on its own 128-byte line,
+// so the arrivals and polls of different candidates go to different L2 lines.
+constexpr int RING_STRIDE = 16;
 
 constexpr double TWO_PI = 2.0 * 3.14159265358979323846;
 constexpr double INV_TWO_PI = 0.15915494309189533577;
@@ -240,14 +243,26 @@ struct Poly {
 // block's time base, reduced mod 1 into a 128-bit fraction:
 //   E3 = f2 h^3/6,  E2 = (f1 + f2 t0) h^2/2,  E1 = (f0 + f1 t0 + f2 t0^2/2) h,
 //   E0 = phi0/(2 pi) + f0 t0 + f1 t0^2/2 + f2 t0^3/6.
-__device__ __forceinline__ u128 poly_term(const double* th, const BlockArgs& b, int k) {
+__device__ __forceinline__ double poly_coef(const double* th, const BlockArgs& b, int k) {
   const double phi0 = th[1], f0 = th[2], f1 = th[3], f2 = th[4];
-  double E;
-  if (k == 3) E = f2 * b.h3_6;
-  else if (k == 2) E = fma(f2, b.t0, f1) * b.h2_2;
-  else if (k == 1) E = fma(f2, b.t0sq_2, fma(f1, b.t0, f0)) * b.h;
-  else E = fma(f2, b.t0cu_6, fma(f1, b.t0sq_2, fma(f0, b.t0, phi0 * INV_TWO_PI)));
-  return frac128(E);
+  if (k == 3) return f2 * b.h3_6;
+  if (k == 2) return fma(f2, b.t0, f1) * b.h2_2;
+  if (k == 1) return fma(f2, b.t0sq_2, fma(f1, b.t0, f0)) * b.h;
+  return fma(f2, b.t0cu_6, fma(f1, b.t0sq_2, fma(f0, b.t0, phi0 * INV_TWO_PI)));
+}
+__device__ __forceinline__ u128 poly_term(const double* th, const BlockArgs& b, int k) {
+  return frac128(poly_coef(th, b, k));
+}
+
+// Inside a lane's run of M consecutive samples k = kc + m' of a tile (kc =
+// k0 + M/2, m' in [-M/2, M/2)), the cubic term E3 k^3 may be folded into the
+// quadratic one as k^2 (E2 + E3 kc), with an error |E3| k^2 |m'| <=
+// |E3| (L - 1)^2 M / 2. A candidate keeps the exact cubic when that bound, in
+// radians, exceeds 2^-24 (below the FP32 rounding of the phase argument
+// itself), i.e. when |E3| (cycles per sample^3) exceeds CUBIC_FOLD_MAX.
+constexpr double CUBIC_FOLD_MAX = 5.9604644775390625e-08 / (6.283185307179586 * (L - 1) * (L - 1) * 0.5 * M);
+__device__ __forceinline__ bool cubic_needed(double E3) {
+  return (__double_as_longlong(E3) & 0x7fffffffffffffffll) > __double_as_longlong(CUBIC_FOLD_MAX);
 }
 
 // x * y mod 2^128 for a 64-bit y.

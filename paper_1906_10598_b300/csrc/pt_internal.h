@@ -22,6 +22,9 @@ namespace pt {
 constexpr int HOST_L = 256;      // samples per tile
 constexpr int HOST_D = 5;        // parameters per candidate
 constexpr int HOST_NP_MAX = 128;
+constexpr int HOST_RING_STRIDE = 16;  // 64-bit words per candidate slot of the DE exchange ring
+// words of one group's DE exchange ring: 3 generations x HOST_NP_MAX candidates
+constexpr size_t RING_GROUP_WORDS = (size_t)3 * HOST_NP_MAX * HOST_RING_STRIDE;
 
 // Per-block constants computed at load time (same meaning as BlockArgs).
 struct HostBlock {
@@ -120,7 +123,7 @@ int check_de_args(pt_ctx* c, const double* bounds, int pop, int gens, double F, 
 // group q solving blocks sched[off[q] .. off[q+1]) of `blocks` (host array,
 // uploaded into `d_desc_buf`, which must hold nblocks descriptors plus the
 // schedule; `mode` says whether to upload them from host memory, to launch,
-// or both). `ring` holds ngroups * 3 * HOST_NP_MAX words; ring and *d_err
+// or both). `ring` holds ngroups * RING_GROUP_WORDS words; ring and *d_err
 // are cleared on `stream` first. Asynchronous.
 constexpr int DE_UPLOAD = 1;  // copy descriptors and schedule to d_desc_buf
 constexpr int DE_LAUNCH = 2;  // clear ring and error word, launch

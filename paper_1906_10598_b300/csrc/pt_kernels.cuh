@@ -104,15 +104,18 @@ __device__ __forceinline__ void prep_zero(unsigned char* cdata, float* negA, int
 // Prepare candidates [0, nc) of `cands` (rows of 5 doubles) padded to npad.
 // The default tier spreads the four FP64 polynomial terms and the amplitude
 // over separate threads so the 1/64-rate FP64 work is spread across all
-// warps of the CTA. Ends with __syncthreads().
+// warps of the CTA, and flags in cub[c] the candidates whose cubic term must
+// stay exact (cubic_needed). Ends with __syncthreads().
 template <int TIER>
 __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs& b, unsigned char* cdata,
-                         float* negA, int* kexp, int kbits) {
+                         float* negA, int* kexp, unsigned char* cub, int kbits) {
   if (TIER == TIER_F64) {
     for (int t = threadIdx.x; t < 5 * npad; t += blockDim.x) {
       const int k = t / npad, c = t - k * npad;
       if (k < 4) {
-        reinterpret_cast<u128*>(cdata + c * CAND_BYTES)[k] = c < nc ? poly_term(cands + c * D, b, k) : (u128)0;
+        const double E = c < nc ? poly_coef(cands + c * D, b, k) : 0.0;
+        reinterpret_cast<u128*>(cdata + c * CAND_BYTES)[k] = frac128(E);
+        if (k == 3) cub[c] = cubic_needed(E) ? 1 : 0;
       } else if (c < nc) {
         const float Af = __double2float_rn(cands[c * D]);
         negA[c] = -Af;
@@ -134,29 +137,79 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
 // ---------------------------------------------------------------------------
 // Work items: one warp, one 256-sample tile, CGV candidates, 8 samples per lane.
 
-// Default tier: 32-bit fixed-point phase walk + FP32 small terms + SFU cosine.
+// Default tier, one candidate, exact cubic: 32-bit fixed-point phase walk
+// u = U0 + k V per sample, FP32 small terms E2 k^2 + E3 k^3, SFU cosine.
+template <bool MASKED>
+__device__ __forceinline__ float cand_exact(const float (&s)[M], uint4 a, float nA, int lane, int nvalid,
+                                            const float (&kk)[M], const float (&kkk)[M]) {
+  const uint32_t V = a.y;
+  uint32_t u = a.x + (uint32_t)(lane * M) * V;
+  const float E2 = __uint_as_float(a.z), E3 = __uint_as_float(a.w);
+  float sum = 0.f;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float q = fmaf(kkk[m], E3, kk[m] * E2);
+    const float x = fmaf((float)(int)u, TWO_PI_2M32, q);
+    const float cv = __cosf(x);
+    float r = fmaf(nA, cv, s[m]);
+    if (MASKED) r = (lane * M + m < nvalid) ? r : 0.f;
+    sum = fmaf(r, r, sum);
+    u += V;
+  }
+  return sum;
+}
+
+// Default tier, one candidate, cubic folded (the candidate is not flagged by
+// cubic_needed): the lane's phase is anchored once at its centre sample kc in
+// fixed point, and its M samples kc + m' follow in FP32 as
+//   x = xc + m' Vc + m'^2 E2c,  xc = 2 pi frac(U0 + kc V) + E2c kc^2,
+//   Vc = 2 pi V + 2 kc E2c,     E2c = E2 + kc E3,
+// two FFMAs with constant m' per sample instead of the fixed-point walk.
+// |x| stays below (1 + M) pi.
+__device__ __forceinline__ float cand_fold(const float (&s)[M], uint4 a, float nA, int lane) {
+  const int kci = lane * M + M / 2;
+  const float kc = (float)kci;
+  const uint32_t V = a.y;
+  const float E2 = __uint_as_float(a.z), E3 = __uint_as_float(a.w);
+  const float E2c = fmaf(E3, kc, E2);
+  const float xc = fmaf((float)(int)(a.x + (uint32_t)kci * V), TWO_PI_2M32, E2c * (kc * kc));
+  const float Vc = fmaf((float)(int)V, TWO_PI_2M32, E2c * (2.0f * kc));
+  float sum = 0.f;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float mp = (float)(m - M / 2);
+    const float x = fmaf(mp, Vc, fmaf(mp * mp, E2c, xc));
+    const float cv = __cosf(x);
+    const float r = fmaf(nA, cv, s[m]);
+    sum = fmaf(r, r, sum);
+  }
+  return sum;
+}
+
+// Default-tier items. A candidate's partial over a tile depends only on the
+// candidate and the tile: full tiles use cand_fold unless the candidate is
+// flagged (flags: its CGV bytes, nonzero = keep the exact cubic), the ragged
+// last tile always uses cand_exact.
 template <int CGV, bool MASKED>
 __device__ __forceinline__ void item_f64(const float (&s)[M], const uint4* anc_i, const float* negA_g, int lane,
                                          int nvalid, const float (&kk)[M], const float (&kkk)[M], float (&acc)[CGV]) {
 #pragma unroll
-  for (int c = 0; c < CGV; ++c) {
-    const uint4 a = anc_i[c];
-    const float nA = negA_g[c];
-    const uint32_t V = a.y;
-    uint32_t u = a.x + (uint32_t)(lane * M) * V;
-    const float E2 = __uint_as_float(a.z), E3 = __uint_as_float(a.w);
-    float sum = 0.f;
+  for (int c = 0; c < CGV; ++c) acc[c] = cand_exact<MASKED>(s, anc_i[c], negA_g[c], lane, nvalid, kk, kkk);
+}
+template <int CGV>
+__device__ __forceinline__ void item_f64_fold(const float (&s)[M], const uint4* anc_i, const float* negA_g, int lane,
+                                              float (&acc)[CGV]) {
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      const float q = fmaf(kkk[m], E3, kk[m] * E2);
-      const float x = fmaf((float)(int)u, TWO_PI_2M32, q);
-      const float cv = __cosf(x);
-      float r = fmaf(nA, cv, s[m]);
-      if (MASKED) r = (lane * M + m < nvalid) ? r : 0.f;
-      sum = fmaf(r, r, sum);
-      u += V;
-    }
-    acc[c] = sum;
+  for (int c = 0; c < CGV; ++c) acc[c] = cand_fold(s, anc_i[c], negA_g[c], lane);
+}
+template <int CGV>
+__device__ __forceinline__ void item_f64_mixed(const float (&s)[M], const uint4* anc_i, const float* negA_g,
+                                               const unsigned char* flags, int lane, const float (&kk)[M],
+                                               const float (&kkk)[M], float (&acc)[CGV]) {
+#pragma unroll
+  for (int c = 0; c < CGV; ++c) {
+    if (flags[c]) acc[c] = cand_exact<false>(s, anc_i[c], negA_g[c], lane, L, kk, kkk);
+    else acc[c] = cand_fold(s, anc_i[c], negA_g[c], lane);
   }
 }
 
@@ -243,6 +296,21 @@ __device__ __forceinline__ void item_f32(const float (&s)[M], const unsigned cha
 // Items a warp evaluates per anchor batch (default tier).
 constexpr int IPB = 4;
 
+// Whether any of the CGV candidates at `f` (16-byte aligned for CGV = 16)
+// carries a cubic_needed flag.
+template <int CGV>
+__device__ __forceinline__ bool any_flag(const unsigned char* f) {
+  if (CGV == 16) {
+    const uint4 w = *reinterpret_cast<const uint4*>(f);
+    return (w.x | w.y | w.z | w.w) != 0u;
+  } else if (CGV == 8) {
+    const uint2 w = *reinterpret_cast<const uint2*>(f);
+    return (w.x | w.y) != 0u;
+  } else {
+    return *reinterpret_cast<const uint32_t*>(f) != 0u;
+  }
+}
+
 // Evaluate candidates [0, ncand) (prepared in cdata/negA/kexp, padded to npad,
 // a multiple of CGV) on the CTA's tiles [tile_begin, tile_begin + ntiles_cta)
 // whose converted samples are s32 / s64 (indexed from tile_begin). Adds the
@@ -254,7 +322,7 @@ constexpr int IPB = 4;
 template <int TIER, int CGV>
 __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int ntiles_cta, const float* s32,
                            const double* s64, const unsigned char* cdata, const float* negA, const int* kexp,
-                           int ncand, int npad, uint4* anc, unsigned long long* acc) {
+                           const unsigned char* cub, int ncand, int npad, uint4* anc, unsigned long long* acc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int G = npad / CGV;
   const int nitems = ntiles_cta * G;
@@ -334,8 +402,12 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int ntiles_ct
         const unsigned char* cd = cdata + g * CGV * CAND_BYTES;
         if (TIER == TIER_F64) {
           const uint4* anc_i = anc_w + k * CGV;
-          if (nvalid == L) item_f64<CGV, false>(s, anc_i, nA, lane, nvalid, kk, kkk, accv);
-          else item_f64<CGV, true>(s, anc_i, nA, lane, nvalid, kk, kkk, accv);
+          if (nvalid == L) {
+            if (any_flag<CGV>(cub + g * CGV)) item_f64_mixed<CGV>(s, anc_i, nA, cub + g * CGV, lane, kk, kkk, accv);
+            else item_f64_fold<CGV>(s, anc_i, nA, lane, accv);
+          } else {
+            item_f64<CGV, true>(s, anc_i, nA, lane, nvalid, kk, kkk, accv);
+          }
         } else if (TIER == TIER_DF32) {
           if (nvalid == L) item_df32<CGV, false>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
           else item_df32<CGV, true>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
@@ -378,7 +450,8 @@ __device__ bool stage_tiles(const BlockArgs& b, int64_t tb, int nt, void* raw, f
 
 // Shared-memory carve-up common to both kernels.
 struct SmemLayout {
-  size_t off_mbar, off_cdata, off_negA, off_kexp, off_acc, off_draw, off_anc, off_samp, off_raw, off_pop, total;
+  size_t off_mbar, off_cdata, off_negA, off_kexp, off_cub, off_acc, off_draw, off_anc, off_samp, off_raw, off_pop,
+      total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -399,6 +472,8 @@ __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, 
   o += align_up((size_t)npad * sizeof(float), 16);
   s.off_kexp = o;
   o += align_up((size_t)npad * sizeof(int), 16);
+  s.off_cub = o;
+  o += align_up((size_t)npad, 16);
   s.off_acc = o;
   o += align_up((size_t)npad * sizeof(unsigned long long), 16);
   s.off_draw = o;
@@ -448,6 +523,7 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   unsigned char* cdata = smem + S.off_cdata;
   float* negA = reinterpret_cast<float*>(smem + S.off_negA);
   int* kexp = reinterpret_cast<int*>(smem + S.off_kexp);
+  unsigned char* cub = smem + S.off_cub;
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem + S.off_acc);
   uint4* anc = reinterpret_cast<uint4*>(smem + S.off_anc);
   float* s32 = reinterpret_cast<float*>(smem + S.off_samp);
@@ -456,9 +532,9 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
 
   const int tid = threadIdx.x;
   if (tid < npad) acc[tid] = 0ull;
-  prep_all<TIER>(a.cands + (int64_t)cb * D, nc, npad, a.b, cdata, negA, kexp, SSE_BITS_OBJ);
+  prep_all<TIER>(a.cands + (int64_t)cb * D, nc, npad, a.b, cdata, negA, kexp, cub, SSE_BITS_OBJ);
   if (!stage_tiles<TIER>(a.b, tb, nt, raw, s32, s64, mbar, a.timeout_ns, a.err)) return;
-  eval_range<TIER, CGV>(a.b, tb, nt, s32, s64, cdata, negA, kexp, nc, npad, anc, acc);
+  eval_range<TIER, CGV>(a.b, tb, nt, s32, s64, cdata, negA, kexp, cub, nc, npad, anc, acc);
   if (tid < nc) atomicAdd(&a.acc[cb + tid], acc[tid]);
 }
 
@@ -490,7 +566,7 @@ struct DeLaunch {
   int ngroups, k;
   int sc_tiles;              // tiles staged per CTA at a time (shared-memory budget)
   int esize_max;             // largest sample size in the launch (shared-memory layout)
-  unsigned long long* ring;  // [ngroups][3][NP_MAX], zeroed by the caller
+  unsigned long long* ring;  // [ngroups][3][NP_MAX][RING_STRIDE], zeroed by the caller
   int* err;                  // zeroed by the caller
   uint64_t timeout_ns;
 };
@@ -501,6 +577,7 @@ struct DeSmem {
   unsigned char* cdata;
   float* negA;
   int* kexp;
+  unsigned char* cub;
   unsigned long long* acc;
   uint32_t *drp, *drt;
   uint4* anc;
@@ -532,14 +609,14 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     return false;
 
   for (int gen = 0; gen <= d.gens; ++gen, ++gg) {
-    unsigned long long* slot = ring + (gg % 3) * NP_MAX;
+    unsigned long long* slot = ring + (gg % 3) * (NP_MAX * RING_STRIDE);
     // the ring slot of the group's next generation was last read before the
     // previous generation ended everywhere: rank 0 clears it, and its fence
     // orders the clear before its own contributions to this generation, which
     // every reader acquires before contributing to the next one
     // (every word of the slot: the group's next block may have a larger population)
     if (rank == 0 && tid < NP_MAX) {
-      ring[((gg + 1) % 3) * NP_MAX + tid] = 0ull;
+      ring[((gg + 1) % 3) * (NP_MAX * RING_STRIDE) + tid * RING_STRIDE] = 0ull;
       __threadfence();
     }
     // trials u of this generation (the initial population at gen 0)
@@ -553,19 +630,20 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     }
     if (tid < npad) sm.acc[tid] = 0ull;
     __syncthreads();
-    prep_all<TIER>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, SSE_BITS_DE);
+    prep_all<TIER>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub, SSE_BITS_DE);
     if (resident) {
-      eval_range<TIER, CGV>(b, tb, nt, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, np, npad, sm.anc, sm.acc);
+      eval_range<TIER, CGV>(b, tb, nt, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad, sm.anc,
+                            sm.acc);
     } else {
       for (int c0 = 0; c0 < nt; c0 += a.sc_tiles) {
         const int cn = min(a.sc_tiles, nt - c0);
         if (!stage_tiles<TIER>(b, tb + c0, cn, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err)) return false;
-        eval_range<TIER, CGV>(b, tb + c0, cn, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, np, npad, sm.anc,
-                              sm.acc);
+        eval_range<TIER, CGV>(b, tb + c0, cn, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
+                              sm.anc, sm.acc);
       }
     }
     if (tid < np) {
-      unsigned long long* w = slot + tid;
+      unsigned long long* w = slot + tid * RING_STRIDE;
       const unsigned long long contrib = (sm.acc[tid] << 8) | 1ull;
       if (rank == 0) {
         // release: orders rank 0's clear of the next slot (by any of its
@@ -637,6 +715,7 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
   sm.cdata = smem + S.off_cdata;
   sm.negA = reinterpret_cast<float*>(smem + S.off_negA);
   sm.kexp = reinterpret_cast<int*>(smem + S.off_kexp);
+  sm.cub = smem + S.off_cub;
   sm.acc = reinterpret_cast<unsigned long long*>(smem + S.off_acc);
   sm.drp = reinterpret_cast<uint32_t*>(smem + S.off_draw);
   sm.drt = sm.drp + NP_MAX;
@@ -650,7 +729,7 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
 
   const int q = blockIdx.x / a.k, rank = blockIdx.x - q * a.k;
   if (q >= a.ngroups) return;
-  unsigned long long* ring = a.ring + (size_t)q * 3 * NP_MAX;
+  unsigned long long* ring = a.ring + (size_t)q * 3 * NP_MAX * RING_STRIDE;
   unsigned long long gg = 0;
   __shared__ DeBlockDesc s_desc;
   for (int e = a.sched_off[q]; e < a.sched_off[q + 1]; ++e) {

@@ -82,7 +82,7 @@ int slot_init(pt_serve_state* S, Slot& sl) {
   PT_CUDA(w, cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
   PT_CUDA(w, cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
   PT_CUDA(w, cudaMalloc(&sl.d_u64, sizeof(unsigned long long)));
-  PT_CUDA(w, cudaMalloc(&sl.d_ring, 3 * HOST_NP_MAX * sizeof(unsigned long long)));
+  PT_CUDA(w, cudaMalloc(&sl.d_ring, RING_GROUP_WORDS * sizeof(unsigned long long)));
   PT_CUDA(w, cudaMalloc(&sl.d_err, sizeof(int)));
   PT_CUDA(w, cudaMalloc(&sl.d_out, 6 * sizeof(double)));
   PT_CUDA(w, cudaMalloc(&sl.d_desc, de_desc_bytes(1, 1)));
