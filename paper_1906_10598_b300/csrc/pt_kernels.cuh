@@ -164,8 +164,8 @@ __device__ __forceinline__ float cand_exact(const float (&s)[M], uint4 a, float 
 // fixed point, and its M samples kc + m' follow in FP32 as
 //   x = xc + m' Vc + m'^2 E2c,  xc = 2 pi frac(U0 + kc V) + E2c kc^2,
 //   Vc = 2 pi V + 2 kc E2c,     E2c = E2 + kc E3,
-// two FFMAs with constant m' per sample instead of the fixed-point walk.
-// |x| stays below (1 + M) pi.
+// two FFMAs with constant m' per sample instead of the fixed-point walk
+// (none at the centre itself). |x| stays below (1 + M) pi.
 __device__ __forceinline__ float cand_fold(const float (&s)[M], uint4 a, float nA, int lane) {
   const int kci = lane * M + M / 2;
   const float kc = (float)kci;
@@ -178,7 +178,7 @@ __device__ __forceinline__ float cand_fold(const float (&s)[M], uint4 a, float n
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const float mp = (float)(m - M / 2);
-    const float x = fmaf(mp, Vc, fmaf(mp * mp, E2c, xc));
+    const float x = (m == M / 2) ? xc : fmaf(mp, Vc, fmaf(mp * mp, E2c, xc));
     const float cv = __cosf(x);
     const float r = fmaf(nA, cv, s[m]);
     sum = fmaf(r, r, sum);
@@ -196,11 +196,26 @@ __device__ __forceinline__ void item_f64(const float (&s)[M], const uint4* anc_i
 #pragma unroll
   for (int c = 0; c < CGV; ++c) acc[c] = cand_exact<MASKED>(s, anc_i[c], negA_g[c], lane, nvalid, kk, kkk);
 }
+// The CGV values -A of an item's candidates (negA_g 16-byte aligned, CGV a
+// multiple of 4), in 16-byte loads.
+template <int CGV>
+__device__ __forceinline__ void load_negA(const float* negA_g, float (&nA)[CGV]) {
+#pragma unroll
+  for (int c = 0; c < CGV; c += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(negA_g + c);
+    nA[c] = v.x;
+    nA[c + 1] = v.y;
+    nA[c + 2] = v.z;
+    nA[c + 3] = v.w;
+  }
+}
 template <int CGV>
 __device__ __forceinline__ void item_f64_fold(const float (&s)[M], const uint4* anc_i, const float* negA_g, int lane,
                                               float (&acc)[CGV]) {
+  float nA[CGV];
+  load_negA<CGV>(negA_g, nA);
 #pragma unroll
-  for (int c = 0; c < CGV; ++c) acc[c] = cand_fold(s, anc_i[c], negA_g[c], lane);
+  for (int c = 0; c < CGV; ++c) acc[c] = cand_fold(s, anc_i[c], nA[c], lane);
 }
 template <int CGV>
 __device__ __forceinline__ void item_f64_mixed(const float (&s)[M], const uint4* anc_i, const float* negA_g,
