@@ -179,6 +179,15 @@ __device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, ui
   *take = m;
 }
 
+// x * 0.5, exactly as the FP64 multiply would round it: when x is normal and
+// x/2 is too, halving only decrements the exponent field (integer pipe);
+// otherwise multiply.
+__device__ __forceinline__ double half_exact(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  return (e > 1 && e < 0x7FF) ? __longlong_as_double(b - (1ll << 52)) : __dmul_rn(x, 0.5);
+}
+
 // Component j of the DE/rand/1/bin trial of individual i from population x
 // (np x 5). FP64 operations use _rn intrinsics so no contraction changes a
 // rounding: the value is bit-identical to a plain IEEE evaluation.
@@ -208,9 +217,9 @@ __device__ __forceinline__ double de_component(const DeControls& dc, const doubl
     }
     if (k != 0.0) v = __dsub_rn(v, __dmul_rn(k, TWO_PI));
   } else if (dkey(v) < dkey(dc.lo[j])) {
-    v = __dmul_rn(__dadd_rn(dc.lo[j], parent), 0.5);
+    v = half_exact(__dadd_rn(dc.lo[j], parent));
   } else if (dkey(v) > dkey(dc.hi[j])) {
-    v = __dmul_rn(__dadd_rn(dc.hi[j], parent), 0.5);
+    v = half_exact(__dadd_rn(dc.hi[j], parent));
   }
   return v;
 }
