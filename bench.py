@@ -152,14 +152,16 @@ def run_reference(args):
 def run_gpu(args):
     import torch
     import paper_1906_10598_b300 as pt
-    from paper_1906_10598_b300 import build
+    from paper_1906_10598_b300 import build, replicas
     rank, world, local = _dist()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    blk = synth.paper400k(rank, gens=args.gens)
+    # one paper-size block per rank (equal costs: the router gives rank r block r)
+    (unit,) = replicas.my_units([1.0] * world, world, rank)
+    blk = synth.paper400k(unit, gens=args.gens)
     ctx = pt.Context(local)
     # a dedicated stream: the library launches on it and the CUDA events below
     # are recorded on it, so they bracket exactly the library's work
@@ -198,10 +200,7 @@ def run_gpu(args):
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(total_ms, device="cuda")
 
     # end to end through the C ABI with host buffers: H2D of the step's samples
     # (pt_load_block) + the fit + D2H of the result, every step
@@ -212,11 +211,7 @@ def run_gpu(args):
         ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
         step()
         e2e_s.append(time.perf_counter() - t)
-    e2e_v = evals / float(np.mean(e2e_s))
-    if world > 1:
-        t = torch.tensor([float(np.mean(e2e_s))], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_v = evals * world / float(t.item())
+    e2e_v = evals * world / replicas.max_over_ranks(float(np.mean(e2e_s)), device="cuda")
 
     value = evals * args.steps * world / (total_ms * 1e-3)
     k_avg = float(np.mean(kern_ms)) * 1e-3
