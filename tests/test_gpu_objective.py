@@ -145,3 +145,27 @@ def test_invalid_arguments(ctx):
         c2.objective(np.zeros((2, 5)))
     assert e.value.code == pt.PT_ENOBLOCK
     c2.close()
+
+
+@pytest.mark.parametrize("f0_frac", [0.2, 0.45])
+def test_phase_generator_error_from_clean_tone(ctx, f0_frac):
+    # A noiseless FP64 tone evaluated at its own parameters: the oracle's SSE is
+    # ~0, the GPU's is sum (A cos phi - A cos phi_hat)^2 ~ A^2 sum sin^2(phi) d^2,
+    # so sqrt(2 SSE / (N A^2)) is the RMS error of the phase generator and
+    # cosine together, over every sample of the block (paper-size block; f0 at
+    # 0.2 fs as in the paper's range, and at 0.45 fs near Nyquist).
+    import paper_1906_10598_b300 as pt
+    n, fs = 400_000, 10_000.0
+    t0 = synth.centred_t0(n, fs)
+    truth = np.array([1.0, 0.7, f0_frac * fs, 4.2, 0.04])
+    s = synth.clean_tone(truth, n, fs, t0)
+    assert oracle.sse(s, fs, t0, truth) < 1e-18 * n
+    ctx.load_block(s, fs, t0)
+    rms = {}
+    for name, tier in (("f64", pt.TIER_F64), ("plain", pt.TIER_PLAIN), ("df32", pt.TIER_DF32), ("f32", pt.TIER_F32)):
+        sse = float(ctx.objective(truth[None, :], tier)[0])
+        rms[name] = np.sqrt(2.0 * sse / (n * truth[0] ** 2))
+    print("phase+cos RMS error (rad):", {k: f"{v:.2e}" for k, v in rms.items()})
+    assert rms["plain"] <= 1e-9
+    assert rms["f64"] <= 1e-6
+    assert rms["df32"] <= 1e-6
