@@ -253,7 +253,8 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
     d.pop_out = h.pop_out;
     d.fit_out = h.fit_out;
     esize_max = std::max(esize_max, h.blk.esize);
-    want = std::max<int64_t>(want, (h.blk.ntiles + k - 1) / k);
+    // a CTA's share of items spans at most one tile more than ntiles / k
+    want = std::max<int64_t>(want, std::min<int64_t>(h.blk.ntiles, (h.blk.ntiles + k - 1) / k + 1));
   }
   char* base = (char*)d_desc_buf;
   if (mode & DE_UPLOAD) {

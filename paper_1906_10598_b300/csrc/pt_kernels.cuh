@@ -327,20 +327,21 @@ __device__ __forceinline__ bool any_flag(const unsigned char* f) {
 }
 
 // Evaluate candidates [0, ncand) (prepared in cdata/negA/kexp, padded to npad,
-// a multiple of CGV) on the CTA's tiles [tile_begin, tile_begin + ntiles_cta)
-// whose converted samples are s32 / s64 (indexed from tile_begin). Adds the
-// fixed-point partial SSE of each candidate into acc[cand] (shared).
-// Items (tile t, group g) = it, it = t * G + g, go to warps round-robin; for
+// a multiple of CGV) on items [item_lo, item_hi) of the tiles staged from
+// tile_begin, whose converted samples are s32 / s64 (indexed from tile_begin).
+// Adds the fixed-point partial SSE of each candidate into acc[cand] (shared).
+// Items (tile t, group g) = it, it = t * G + g (t counted from tile_begin),
+// go to warps round-robin; for
 // the default tier each warp computes the tile anchors of its next IPB items
 // itself into its own slice of `anc` (IPB * CGV entries per warp), so no
 // CTA-wide barrier separates anchors from evaluation. Ends with __syncthreads().
 template <int TIER, int CGV>
-__device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int ntiles_cta, const float* s32,
+__device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, int item_hi, const float* s32,
                            const double* s64, const unsigned char* cdata, const float* negA, const int* kexp,
                            const unsigned char* cub, int ncand, int npad, uint4* anc, unsigned long long* acc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int G = npad / CGV;
-  const int nitems = ntiles_cta * G;
+  const int nitems = item_hi;
   float kk[M], kkk[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
@@ -353,7 +354,7 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int ntiles_ct
   uint4* anc_w = anc + warp * (IPB * CGV);
   constexpr int LPC = 32 / CGV;  // lanes holding each candidate's warp sum
 
-  for (int base = warp; base < nitems; base += nw * IPB) {
+  for (int base = item_lo + warp; base < nitems; base += nw * IPB) {
     if (TIER == TIER_F64) {
       for (int q = lane; q < IPB * CGV; q += 32) {
         const int k = q / CGV, c = q - k * CGV;
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   if (tid < npad) acc[tid] = 0ull;
   prep_all<TIER>(a.cands + (int64_t)cb * D, nc, npad, a.b, cdata, negA, kexp, cub, SSE_BITS_OBJ);
   if (!stage_tiles<TIER>(a.b, tb, nt, raw, s32, s64, mbar, a.timeout_ns, a.err)) return;
-  eval_range<TIER, CGV>(a.b, tb, nt, s32, s64, cdata, negA, kexp, cub, nc, npad, anc, acc);
+  eval_range<TIER, CGV>(a.b, tb, 0, nt * (npad / CGV), s32, s64, cdata, negA, kexp, cub, nc, npad, anc, acc);
   if (tid < nc) atomicAdd(&a.acc[cb + tid], acc[tid]);
 }
 
@@ -616,8 +617,15 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
   const int tid = threadIdx.x;
   const int np = d.np, npad = (d.np + CGV - 1) / CGV * CGV;
   const BlockArgs& b = d.b;
-  const int64_t tb = (int64_t)rank * b.ntiles / k;
-  const int nt = (int)((int64_t)(rank + 1) * b.ntiles / k - tb);
+  // this CTA's share of the block's items (tile, candidate group), in tile
+  // order: item-exact, so the CTAs' shares differ by at most one item; it
+  // spans the staged tiles [tb, tb + nt), items [ilo, ihi) counted from tb
+  const int G = npad / CGV;
+  const int64_t nitems = b.ntiles * G;
+  const int64_t it0 = (int64_t)rank * nitems / k, it1 = (int64_t)(rank + 1) * nitems / k;
+  const int64_t tb = it0 / G;
+  const int nt = it1 > it0 ? (int)((it1 - 1) / G - tb + 1) : 0;
+  const int ilo = (int)(it0 - tb * G), ihi = (int)(it1 - tb * G);
   const bool resident = nt <= a.sc_tiles;
   const unsigned long long arrived = (unsigned long long)(k & 0xff);
   if (resident && nt > 0 && !stage_tiles<TIER>(b, tb, nt, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err))
@@ -647,13 +655,14 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     __syncthreads();
     prep_all<TIER>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub, SSE_BITS_DE);
     if (resident) {
-      eval_range<TIER, CGV>(b, tb, nt, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad, sm.anc,
+      eval_range<TIER, CGV>(b, tb, ilo, ihi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad, sm.anc,
                             sm.acc);
     } else {
       for (int c0 = 0; c0 < nt; c0 += a.sc_tiles) {
         const int cn = min(a.sc_tiles, nt - c0);
+        const int lo = max(ilo, c0 * G) - c0 * G, hi = min(ihi, (c0 + cn) * G) - c0 * G;
         if (!stage_tiles<TIER>(b, tb + c0, cn, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err)) return false;
-        eval_range<TIER, CGV>(b, tb + c0, cn, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
+        eval_range<TIER, CGV>(b, tb + c0, lo, hi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
                               sm.anc, sm.acc);
       }
     }
