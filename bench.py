@@ -314,7 +314,7 @@ def run_batch(args):
                        "group_ctas": info["group_ctas"], "groups": info["ngroups"],
                        "uses_graph": info["uses_graph"], "autotune_predicted_ms": info["predicted_ms"],
                        "tune_rate_per_cta": info["tune_rate"], "tune_gen_us": info["tune_gen_us"],
-                       "tune_sync_us": info["tune_sync_us"], "create_s": create_s},
+                       "tune_rate_stream_per_cta": info["tune_rate_stream"], "create_s": create_s},
             "blocks_per_s": len(blocks) / mean_s,
             "roofline": {"bound": "alu", "achieved": evals / mean_s, "peak": SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6,
                          "unit": UNIT, "frac": evals / mean_s / (SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6),

@@ -185,9 +185,9 @@ typedef struct pt_batch_info {
   double sample_evals;  /* sum over blocks of n * pop * (gens + 1) */
   double predicted_ms;  /* the autotuner's makespan estimate */
   double last_ms;       /* device time of the last pt_batch_run */
-  double tune_rate;     /* calibrated objective sample-evals/s per CTA */
+  double tune_rate;     /* calibrated objective sample-evals/s per CTA, tiles resident */
   double tune_gen_us;   /* calibrated fixed cost per generation (us) */
-  double tune_sync_us;  /* calibrated extra cost per generation when a block spans CTAs (us) */
+  double tune_rate_stream; /* calibrated sample-evals/s per CTA, tiles staged chunk by chunk */
 } pt_batch_info;
 
 /* Copy the blocks to the device, choose the launch shape and capture it.

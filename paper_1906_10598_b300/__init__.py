@@ -210,7 +210,7 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("nblocks", ctypes.c_int), ("ngroups", ctypes.c_int), ("group_ctas", ctypes.c_int),
                 ("tier", ctypes.c_int), ("uses_graph", ctypes.c_int), ("sample_evals", ctypes.c_double),
                 ("predicted_ms", ctypes.c_double), ("last_ms", ctypes.c_double), ("tune_rate", ctypes.c_double),
-                ("tune_gen_us", ctypes.c_double), ("tune_sync_us", ctypes.c_double)]
+                ("tune_gen_us", ctypes.c_double), ("tune_rate_stream", ctypes.c_double)]
 
 
 def _batch_protos(lib):

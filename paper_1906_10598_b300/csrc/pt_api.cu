@@ -46,18 +46,7 @@ bool valid_tier(int t) { return t >= PT_TIER_F64 && t <= PT_TIER_F32; }
 
 // Candidates per work item for the default tier: the width in {16, 8, 4}
 // that pads `n` the least (wider on ties); the other tiers use 8.
-int pick_cg(int tier, int n) {
-  if (tier != PT_TIER_F64) return 8;
-  int best = 16, best_pad = (n + 15) / 16 * 16;
-  for (int cg : {8, 4}) {
-    const int pad = (n + cg - 1) / cg * cg;
-    if (pad < best_pad) {
-      best = cg;
-      best_pad = pad;
-    }
-  }
-  return best;
-}
+int pick_cg(int tier, int n) { return tier == PT_TIER_F64 ? pick_cg_f64(n) : 8; }
 
 namespace {
 

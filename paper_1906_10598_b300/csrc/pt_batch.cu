@@ -2,11 +2,15 @@
 // cooperative launch over groups of CTAs, replayed from a captured CUDA graph.
 //
 // Autotuner: the per-generation time of one block on k CTAs is modelled as
-//   t(k) = ceil(ntiles / k) * 256 * npad / R + c_gen + [k > 1] c_sync,
-// with R the objective rate of one CTA, c_gen the fixed per-generation cost
-// (trial generation, FP64 set-up, selection) and c_sync the extra cost of the
-// cross-CTA exchange. R, c_gen and c_sync are calibrated with short DE runs on
-// the batch's first block and cached in the context. For each candidate group
+//   t(k) = ceil(ntiles / k) * 256 * npad / R + c_gen,
+// with R the objective rate of one CTA (R_res while a CTA's tiles fit its
+// shared memory, R_stream when they are staged chunk by chunk each
+// generation) and c_gen the fixed per-generation cost (trial generation, FP64
+// set-up, exchange, selection). R_res and c_gen come from short DE runs of the
+// batch's first block at its own population on two group sizes that keep the
+// tiles resident (the work per CTA differs, nothing else); R_stream from a
+// third run with about three times the resident capacity per CTA, when the
+// block is that large. They are cached in the context. For each candidate group
 // size k the blocks are assigned longest-first to the least-loaded of the
 // floor(SMs / k) groups (LPT); the k with the shortest predicted makespan wins.
 #include <cuda_runtime.h>
@@ -74,35 +78,53 @@ int npad_of(int tier, int pop) {
   return (pop + cg - 1) / cg * cg;
 }
 
-// Calibrate R, c_gen, c_sync (cached in the context per tier-independent rates).
+// Samples one CTA of a group of k evaluates per generation.
+double cta_samples(int64_t ntiles, int k) { return (double)((ntiles + k - 1) / k) * HOST_L; }
+
+// Whether one CTA of a group of k keeps its share of the block resident (its
+// item share spans at most one tile more than ntiles / k).
+bool resident(const pt_ctx* c, int64_t ntiles, int k) { return (ntiles + k - 1) / k + 1 <= c->tune_res_tiles; }
+
+int clamp_k(const pt_ctx* c, int64_t k) { return (int)std::max<int64_t>(1, std::min<int64_t>(k, c->sms)); }
+
+// Calibrate R_res, R_stream and c_gen (cached in the context).
 int calibrate(pt_ctx* c, int tier, const HostDeBlock& b0) {
   if (c->tuned) return PT_OK;
-  HostDeBlock b = b0;
+  const HostDeBlock& b = b0;
   const int64_t nt = b.blk.ntiles;
-  double t_full, t_small, t_k;
+  const double np = (double)npad_of(tier, b.pop);
+  const int S = pick_sc_tiles(c, tier, b.blk.esize, 96);
+  c->tune_res_tiles = S;
+  // two resident shapes: about S/3 and 2S/3 tiles per CTA
+  int ka = clamp_k(c, (nt + std::max(1, S / 3) - 1) / std::max(1, S / 3));
+  int kb = clamp_k(c, (nt + std::max(1, 2 * S / 3) - 1) / std::max(1, 2 * S / 3));
+  if (kb >= ka) kb = std::max(1, ka / 2);
+  double ta, tb;
   int rc;
-  if ((rc = time_per_gen(c, tier, b, 1, &t_full)) != PT_OK) return rc;
-  HostDeBlock bs = b;
-  bs.pop = 8;
-  if ((rc = time_per_gen(c, tier, bs, 1, &t_small)) != PT_OK) return rc;
-  const int kk = (int)std::min<int64_t>(4, nt);
-  if ((rc = time_per_gen(c, tier, b, kk, &t_k)) != PT_OK) return rc;
-  const double W = (double)nt * HOST_L;
-  const double dn = (double)(npad_of(tier, b.pop) - npad_of(tier, 8));
-  double R = dn > 0 && t_full > t_small ? W * dn / (t_full - t_small) : W * npad_of(tier, b.pop) / t_full;
-  double cg = std::max(0.0, t_full - W * npad_of(tier, b.pop) / R);
-  const double Wk = (double)((nt + kk - 1) / kk) * HOST_L;
-  double cs = std::max(0.0, t_k - (Wk * npad_of(tier, b.pop) / R + cg));
+  // the context's first DE launch also loads the module: run one untimed first
+  if ((rc = time_per_gen(c, tier, b, ka, &ta)) != PT_OK) return rc;
+  if ((rc = time_per_gen(c, tier, b, ka, &ta)) != PT_OK) return rc;
+  if ((rc = time_per_gen(c, tier, b, kb, &tb)) != PT_OK) return rc;
+  const double wa = cta_samples(nt, ka), wb = cta_samples(nt, kb);
+  const double R = (wb > wa && tb > ta) ? (wb - wa) * np / (tb - ta) : wa * np / ta;
+  const double cg = std::max(0.0, ta - wa * np / R);
+  double Rs = R;
+  if (nt >= 3 * (int64_t)S) {
+    const int ks = clamp_k(c, nt / (3 * (int64_t)S));
+    double ts;
+    if ((rc = time_per_gen(c, tier, b, ks, &ts)) != PT_OK) return rc;
+    if (ts > cg) Rs = cta_samples(nt, ks) * np / (ts - cg);
+  }
   c->tune_rate = R;
+  c->tune_rate_stream = Rs;
   c->tune_fixed_s = cg;
-  c->tune_sync_s = cs;
   c->tuned = true;
   return PT_OK;
 }
 
 double block_seconds(const pt_ctx* c, int tier, const HostDeBlock& b, int k) {
-  const double W = (double)((b.blk.ntiles + k - 1) / k) * HOST_L;
-  const double per_gen = W * npad_of(tier, b.pop) / c->tune_rate + c->tune_fixed_s + (k > 1 ? c->tune_sync_s : 0.0);
+  const double R = resident(c, b.blk.ntiles, k) ? c->tune_rate : c->tune_rate_stream;
+  const double per_gen = cta_samples(b.blk.ntiles, k) * npad_of(tier, b.pop) / R + c->tune_fixed_s;
   return per_gen * (b.gens + 1);
 }
 
@@ -242,7 +264,7 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
   std::vector<int> ks;
   if (group_ctas > 0) ks.push_back(std::min(group_ctas, c->sms));
   else
-    for (int k : {1, 2, 4, 8, 16, 37, 74})
+    for (int k : {1, 2, 4, 8, 16, 37, 74, 148})
       if (k <= c->sms) ks.push_back(k);
   double best = 1e300;
   for (int k : ks) {
@@ -341,7 +363,7 @@ int pt_batch_get_info(const pt_batch* b, pt_batch_info* info) {
   info->last_ms = b->last_ms;
   info->tune_rate = b->ctx->tune_rate;
   info->tune_gen_us = b->ctx->tune_fixed_s * 1e6;
-  info->tune_sync_us = b->ctx->tune_sync_s * 1e6;
+  info->tune_rate_stream = b->ctx->tune_rate_stream;
   return PT_OK;
 }
 

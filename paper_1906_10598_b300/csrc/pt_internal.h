@@ -84,7 +84,9 @@ struct pt_ctx {
   float last_ms = 0.f;
   uint64_t timeout_ns = 2000000000ull;
   // autotune cache of the batched launcher: per-CTA rate and per-generation costs
-  double tune_rate = 0.0, tune_fixed_s = 0.0, tune_sync_s = 0.0;
+  double tune_rate = 0.0, tune_fixed_s = 0.0;
+  double tune_rate_stream = 0.0;  // per-CTA rate when a CTA's tiles are staged chunk by chunk
+  int tune_res_tiles = 0;         // tiles one CTA keeps resident (its shared-memory capacity)
   bool tuned = false;
   pt_serve_state* serve = nullptr;
 };

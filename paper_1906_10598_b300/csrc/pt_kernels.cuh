@@ -308,6 +308,26 @@ __device__ __forceinline__ void item_f32(const float (&s)[M], const unsigned cha
   }
 }
 
+// Candidates per work item of the default tier for a batch of n candidates:
+// the width in {16, 8, 4} with the least padded work, each padded candidate
+// weighted by the measured cost per candidate of its width on B300 (narrower
+// items amortise the per-item anchor loads, reduction and loop over fewer
+// candidates: 1.0, 1.1 and 1.4 for 16, 8 and 4).
+inline int pick_cg_f64(int n) {
+  int best = 16;
+  double best_cost = (double)((n + 15) / 16 * 16);
+  const int widths[2] = {8, 4};
+  const double weight[2] = {1.1, 1.4};
+  for (int i = 0; i < 2; ++i) {
+    const double cost = (double)((n + widths[i] - 1) / widths[i] * widths[i]) * weight[i];
+    if (cost < best_cost) {
+      best = widths[i];
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
 // Items a warp evaluates per anchor batch (default tier).
 constexpr int IPB = 4;
 

@@ -88,14 +88,7 @@ int launch_any(int tier, const BlockArgs& b, const double* cands, int ncand, uns
   if (tier == PT_TIER_PLAIN) return launch<TIER_PLAIN, 8>(b, cands, ncand, acc, err, s, sms, optin);
   if (tier == PT_TIER_DF32) return launch<TIER_DF32, 8>(b, cands, ncand, acc, err, s, sms, optin);
   if (tier == PT_TIER_F32) return launch<TIER_F32, 8>(b, cands, ncand, acc, err, s, sms, optin);
-  const int n = std::min(ncand, NP_MAX);
-  // same item width rule as pt_objective: the width in {16, 8, 4} padding n least
-  int cg = 16, pad = (n + 15) / 16 * 16;
-  if ((n + 7) / 8 * 8 < pad) {
-    cg = 8;
-    pad = (n + 7) / 8 * 8;
-  }
-  if ((n + 3) / 4 * 4 < pad) cg = 4;
+  const int cg = pick_cg_f64(std::min(ncand, NP_MAX));  // the item width pt_objective uses
   if (cg == 16) return launch<TIER_F64, 16>(b, cands, ncand, acc, err, s, sms, optin);
   if (cg == 8) return launch<TIER_F64, 8>(b, cands, ncand, acc, err, s, sms, optin);
   return launch<TIER_F64, 4>(b, cands, ncand, acc, err, s, sms, optin);
