@@ -40,6 +40,36 @@ UNIT = "sample-evals/s"
 PAPER_SAMPLE_EVALS_PER_S = 400_000 * 80_000 / 6.5
 # SFU-bound roofline: 148 SMs x 16 cosine ops/clk/SM x 2032 MHz, one cosine per sample-eval
 SMS, SFU_PER_CLK, SM_MAX_MHZ = 148, 16, 2032.0
+# ncu summary of the DE kernel: its DRAM bytes per launch and the sources it was taken on
+PROFILE = os.path.join(ROOT, "profiles", "k_de_paper400k_full.md")
+KERNEL_SOURCES = ("pt_kernels.cuh", "pt_device.cuh")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1906_10598_b300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """(DRAM bytes per launch, note) from the committed ncu summary, or (None,
+    why) when the kernel sources changed since that capture."""
+    try:
+        fields = {}
+        with open(PROFILE) as fh:
+            for line in fh:
+                if ":" in line and line.startswith(("traffic_bytes_per_launch", "kernel_sources_sha256")):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel_sources_sha256") != kernel_sources_sha256():
+            return None, "kernel sources changed since the ncu capture"
+        return int(fields["traffic_bytes_per_launch"]), "ncu dram__bytes_read + write, one launch (" + \
+            os.path.basename(PROFILE) + ")"
+    except (OSError, KeyError, ValueError):
+        return None, "no ncu summary"
 
 
 def _dist():
@@ -217,8 +247,9 @@ def run_gpu(args):
     k_avg = float(np.mean(kern_ms)) * 1e-3
     achieved = evals / k_avg
     peak = SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6
+    traffic, traffic_note = profiled_traffic()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-            "traffic": None, "kernel": "k_de<TIER_F64>",
+            "traffic": traffic, "traffic_note": traffic_note, "kernel": "k_de<TIER_F64>",
             "peak_basis": "148 SMs x 16 SFU cosines/clk x 2032 MHz (one cosine per sample-eval)"}
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (SMS * SFU_PER_CLK * clocks["sm_mhz"] * 1e6)
