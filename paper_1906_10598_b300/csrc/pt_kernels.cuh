@@ -137,24 +137,34 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
 // ---------------------------------------------------------------------------
 // Work items: one warp, one 256-sample tile, CGV candidates, 8 samples per lane.
 
-// Default tier, one candidate, exact cubic: 32-bit fixed-point phase walk
-// u = U0 + k V per sample, FP32 small terms E2 k^2 + E3 k^3, SFU cosine.
+// Default tier, one candidate, exact cubic: the lane's phase is anchored at
+// its centre sample kc in fixed point, and its M samples kc + m' follow in
+// FP32 from the exact expansion of the small terms about kc,
+//   E2 k^2 + E3 k^3 = S0 + m' S1 + m'^2 S2 + m'^3 E3,
+//   S0 = E2 kc^2 + E3 kc^3,  S1 = 2 E2 kc + 3 E3 kc^2,  S2 = E2 + 3 E3 kc,
+// so x = xc + m' Vc + m'^2 S2 + m'^3 E3 with xc = 2 pi frac(U0 + kc V) + S0
+// and Vc = 2 pi V + S1: three FFMAs per sample (none at the centre). MASKED
+// zeroes the residuals of samples at or past nvalid (the ragged last tile).
 template <bool MASKED>
-__device__ __forceinline__ float cand_exact(const float (&s)[M], uint4 a, float nA, int lane, int nvalid,
-                                            const float (&kk)[M], const float (&kkk)[M]) {
+__device__ __forceinline__ float cand_exact(const float (&s)[M], uint4 a, float nA, int lane, int nvalid) {
+  const int kci = lane * M + M / 2;
+  const float kc = (float)kci, kc2 = kc * kc;
   const uint32_t V = a.y;
-  uint32_t u = a.x + (uint32_t)(lane * M) * V;
   const float E2 = __uint_as_float(a.z), E3 = __uint_as_float(a.w);
+  const float S0 = fmaf(E3, kc2 * kc, E2 * kc2);
+  const float S1 = fmaf(E3, 3.0f * kc2, E2 * (2.0f * kc));
+  const float S2 = fmaf(E3, 3.0f * kc, E2);
+  const float xc = fmaf((float)(int)(a.x + (uint32_t)kci * V), TWO_PI_2M32, S0);
+  const float Vc = fmaf((float)(int)V, TWO_PI_2M32, S1);
   float sum = 0.f;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const float q = fmaf(kkk[m], E3, kk[m] * E2);
-    const float x = fmaf((float)(int)u, TWO_PI_2M32, q);
+    const float mp = (float)(m - M / 2);
+    const float x = (m == M / 2) ? xc : fmaf(mp, Vc, fmaf(mp * mp, S2, fmaf(mp * mp * mp, E3, xc)));
     const float cv = __cosf(x);
     float r = fmaf(nA, cv, s[m]);
     if (MASKED) r = (lane * M + m < nvalid) ? r : 0.f;
     sum = fmaf(r, r, sum);
-    u += V;
   }
   return sum;
 }
@@ -192,9 +202,9 @@ __device__ __forceinline__ float cand_fold(const float (&s)[M], uint4 a, float n
 // last tile always uses cand_exact.
 template <int CGV, bool MASKED>
 __device__ __forceinline__ void item_f64(const float (&s)[M], const uint4* anc_i, const float* negA_g, int lane,
-                                         int nvalid, const float (&kk)[M], const float (&kkk)[M], float (&acc)[CGV]) {
+                                         int nvalid, float (&acc)[CGV]) {
 #pragma unroll
-  for (int c = 0; c < CGV; ++c) acc[c] = cand_exact<MASKED>(s, anc_i[c], negA_g[c], lane, nvalid, kk, kkk);
+  for (int c = 0; c < CGV; ++c) acc[c] = cand_exact<MASKED>(s, anc_i[c], negA_g[c], lane, nvalid);
 }
 // The CGV values -A of an item's candidates (negA_g 16-byte aligned, CGV a
 // multiple of 4), in 16-byte loads.
@@ -219,11 +229,10 @@ __device__ __forceinline__ void item_f64_fold(const float (&s)[M], const uint4* 
 }
 template <int CGV>
 __device__ __forceinline__ void item_f64_mixed(const float (&s)[M], const uint4* anc_i, const float* negA_g,
-                                               const unsigned char* flags, int lane, const float (&kk)[M],
-                                               const float (&kkk)[M], float (&acc)[CGV]) {
+                                               const unsigned char* flags, int lane, float (&acc)[CGV]) {
 #pragma unroll
   for (int c = 0; c < CGV; ++c) {
-    if (flags[c]) acc[c] = cand_exact<false>(s, anc_i[c], negA_g[c], lane, L, kk, kkk);
+    if (flags[c]) acc[c] = cand_exact<false>(s, anc_i[c], negA_g[c], lane, L);
     else acc[c] = cand_fold(s, anc_i[c], negA_g[c], lane);
   }
 }
@@ -362,13 +371,6 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int G = npad / CGV;
   const int nitems = item_hi;
-  float kk[M], kkk[M];
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    const int k = lane * M + m;
-    kk[m] = (float)(k * k);
-    kkk[m] = (float)(k * k * k);
-  }
   const dfloat t0d = df_from_double(b.t0), hd = df_from_double(b.h);
   const float t0f = __double2float_rn(b.t0), hf = __double2float_rn(b.h);
   uint4* anc_w = anc + warp * (IPB * CGV);
@@ -439,10 +441,10 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
         if (TIER == TIER_F64) {
           const uint4* anc_i = anc_w + k * CGV;
           if (nvalid == L) {
-            if (any_flag<CGV>(cub + g * CGV)) item_f64_mixed<CGV>(s, anc_i, nA, cub + g * CGV, lane, kk, kkk, accv);
+            if (any_flag<CGV>(cub + g * CGV)) item_f64_mixed<CGV>(s, anc_i, nA, cub + g * CGV, lane, accv);
             else item_f64_fold<CGV>(s, anc_i, nA, lane, accv);
           } else {
-            item_f64<CGV, true>(s, anc_i, nA, lane, nvalid, kk, kkk, accv);
+            item_f64<CGV, true>(s, anc_i, nA, lane, nvalid, accv);
           }
         } else if (TIER == TIER_DF32) {
           if (nvalid == L) item_df32<CGV, false>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
