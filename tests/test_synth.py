@@ -1,0 +1,58 @@
+"""Pins of the synthetic workloads' ground truth (CPU).
+
+The serving workload's per-block truth is the cubic Taylor expansion of each
+stream's continuous phase about the block centre (Eq. 2-2-3). Its truncation
+error must respect the Lagrange bound of Eq. 3-2-2 at every sample of the
+block, with n = 3:
+    |R_3(t)| <= max |phi''''| |t - tc|^4 / 4!   (t - tc up to T/2).
+A wrong sign or factor in any re-centred coefficient leaves a residual of
+order |t - tc|, |t - tc|^2 or |t - tc|^3, far above that bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+
+@pytest.mark.parametrize("index", [0, 3, 17])
+def test_stream_taylor_truth_within_lagrange_bound_eq_3_2_2(index):
+    for spec in synth.make_streams(seed=5):
+        n = int(round(spec.block_s * spec.fs))
+        start = index * n
+        tc = (start + (n - 1) / 2.0) / spec.fs
+        tau = (np.arange(n, dtype=np.float64) - (n - 1) / 2.0) / spec.fs
+        truth = synth.stream_taylor_truth(spec, tc)
+        # the stream's phase in cycles relative to the centre, and the cubic model
+        p = synth.stream_phase_cycles(spec, tc + tau) - synth.stream_phase_cycles(spec, np.array([tc]))[0]
+        model = truth[2] * tau + truth[3] * tau ** 2 / 2 + truth[4] * tau ** 3 / 6
+        resid = np.abs(p - model)
+        w = 2 * math.pi / spec.dop_p
+        d4max = abs(spec.F3) + spec.dop_a * w ** 4  # |phi''''| in cycles/s^4, bound over the block
+        bound = d4max * np.abs(tau) ** 4 / 24.0
+        # cancellation in p (tens of thousands of cycles) limits the comparison to ~1e-9 cycles
+        assert np.all(resid <= bound * (1 + 1e-9) + 1e-8), (spec.stream_id, float(np.max(resid - bound)))
+        # and the border value matches Eq. 3-2-2's form |phi''''| T^4 / (2^4 4!)
+        T = n / spec.fs
+        assert resid.max() <= d4max * T ** 4 / (16 * 24) + 1e-8
+        # the truth's phase is the stream's phase at the centre, wrapped to [-pi, pi)
+        p0 = float(synth.stream_phase_cycles(spec, np.array([tc]))[0])
+        assert math.isclose(math.remainder(truth[1] - 2 * math.pi * p0, 2 * math.pi), 0.0, abs_tol=1e-9)
+
+
+def test_stream_taylor_truth_catches_a_wrong_coefficient():
+    # the bound is tight enough to reject a perturbed linear or quadratic term
+    spec = synth.make_streams(seed=5)[1]
+    n = int(round(spec.block_s * spec.fs))
+    tc = ((n - 1) / 2.0) / spec.fs
+    tau = (np.arange(n, dtype=np.float64) - (n - 1) / 2.0) / spec.fs
+    truth = synth.stream_taylor_truth(spec, tc)
+    p = synth.stream_phase_cycles(spec, tc + tau) - synth.stream_phase_cycles(spec, np.array([tc]))[0]
+    w = 2 * math.pi / spec.dop_p
+    bound = (abs(spec.F3) + spec.dop_a * w ** 4) * np.abs(tau) ** 4 / 24.0 + 1e-8
+    for j, scale in ((2, 1e-6), (3, 1e-3), (4, 1e-2)):
+        t2 = truth.copy()
+        t2[j] += scale * (abs(t2[j]) + 1.0)
+        model = t2[2] * tau + t2[3] * tau ** 2 / 2 + t2[4] * tau ** 3 / 6
+        assert np.any(np.abs(p - model) > bound), j
