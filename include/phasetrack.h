@@ -281,6 +281,70 @@ PT_API int pt_warm_bounds(const double prev[5], double dt, double T_next, double
 PT_API int pt_continuity(const double a[5], double Ta, const double b[5], double Tb, double max_dphi,
                          double max_dfreq, double* dphi, double* dfreq);
 
+/* ---- Block-to-block tracking of one stream ----------------------------------
+ * The data process flow of Sec. 3.1.4 for one station stream cut into
+ * contiguous blocks, each fitted about its own centre (t0 = -(n-1)/(2 fs)):
+ *   - ranges: the first block takes the session's initial bounds; each later
+ *     block takes the running-time ranges of Sec. 3.1.1 (pt_warm_bounds)
+ *     extrapolated from the last accepted fit over the time between centres;
+ *   - acceptance: the continuity check of Eq. 3-1-2 (pt_continuity) against
+ *     the previous block when that block was accepted (the first block, and a
+ *     block after an abandoned one, have no adjacent reference and are
+ *     accepted unchecked);
+ *   - retry: a rejected fit is searched again with the f0, f1, f2 half-widths
+ *     multiplied by `enlarge` and A widened by the same factor (phi0 keeps the
+ *     full circle), with a new DE seed; after `max_attempts` searches the
+ *     block is abandoned (the paper abandons it after three, Sec. 3.1.4);
+ *   - observables: the border phase and frequency (Eq. 3-1-2), the block's
+ *     total phase phi(T/2) - phi(-T/2) and, over each count interval T_c of
+ *     accepted contiguous blocks, the integration Doppler
+ *     Phi_total / T_c (Eq. 4-1-2); an abandoned block breaks the interval.
+ * The paper's output record (Appendix 1) carries a data quality index it does
+ * not define; here it is the number of the search that was accepted (1 = the
+ * first), or 0 for an abandoned block. */
+typedef struct pt_track pt_track;
+
+typedef struct pt_track_config {
+  int pop, gens;           /* DE controls of every search (Table 3-1-1) */
+  double F, CR;
+  uint64_t seed;           /* search k of block i uses Philox key seed + k, block id i */
+  int tier;                /* PT_TIER_* */
+  double max_dphi;         /* continuity threshold on the border phase (rad), > 0 */
+  double max_dfreq;        /* continuity threshold on the border frequency (rad/s), > 0 */
+  double enlarge;          /* range factor per retry, >= 1 */
+  int max_attempts;        /* searches per block, >= 1 (the paper: 3) */
+  double count_interval;   /* T_c of the integration Doppler (s); <= 0 disables it */
+} pt_track_config;
+
+typedef struct pt_track_result {
+  int64_t block_index;     /* 0, 1, ... in submission order */
+  int quality;             /* accepted search (1..max_attempts), 0 = abandoned */
+  int attempts;            /* searches made for this block */
+  double params[5];        /* accepted (A, phi0, f0, f1, f2) about the block centre; the last search's if abandoned */
+  double sse;
+  double dphi, dfreq;      /* continuity residuals of the accepted search (NaN if unchecked) */
+  double phi_left, phi_right;  /* border phase mod 2 pi (rad) at -T/2 and T/2 */
+  double f_left, f_right;      /* border frequency (rad/s) */
+  double total_phase;      /* phi(T/2) - phi(-T/2) (rad), the Eq. 4-1-2 term; NaN if abandoned */
+  double int_doppler;      /* Phi_total / T_c (rad/s) when this block completes a count interval, else NaN */
+  double interval_phase;   /* Phi_total of that interval (rad), else NaN */
+} pt_track_result;
+
+/* Start a session on ctx (which it uses for every fit; one session per
+ * context at a time). bounds: the first block's (lo, hi) pairs for A, phi0,
+ * f0, f1, f2 (host pointer, 10 doubles). Errors: PT_EINVAL, PT_ENOMEM. */
+PT_API int pt_track_create(pt_ctx* ctx, const pt_track_config* cfg, const double bounds[10], pt_track** out);
+
+/* Fit the stream's next block (samples as in pt_load_block, the context's
+ * current block is replaced), synchronously; *out is always written when the
+ * return is PT_OK, which it is also for an abandoned block (quality 0).
+ * Errors: PT_EINVAL (bad arguments), and those of pt_load_block and
+ * pt_de_solve_ex, which leave the session unchanged. */
+PT_API int pt_track_block(pt_track* tr, const void* samples, int64_t n, int dtype, double scale, double fs,
+                          pt_track_result* out);
+
+PT_API void pt_track_destroy(pt_track* tr);
+
 /* ---- Objective without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for host
  * programs that must not allocate device memory on their call path, such as

@@ -407,3 +407,76 @@ class Server:
 
     def clock(self) -> float:
         return float(self._lib.pt_clock())
+
+
+class TrackConfig(ctypes.Structure):
+    """Mirror of ``pt_track_config``."""
+    _fields_ = [("pop", ctypes.c_int), ("gens", ctypes.c_int), ("F", ctypes.c_double), ("CR", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("tier", ctypes.c_int), ("max_dphi", ctypes.c_double),
+                ("max_dfreq", ctypes.c_double), ("enlarge", ctypes.c_double), ("max_attempts", ctypes.c_int),
+                ("count_interval", ctypes.c_double)]
+
+
+class TrackResult(ctypes.Structure):
+    """Mirror of ``pt_track_result``."""
+    _fields_ = [("block_index", ctypes.c_int64), ("quality", ctypes.c_int), ("attempts", ctypes.c_int),
+                ("params", ctypes.c_double * 5), ("sse", ctypes.c_double), ("dphi", ctypes.c_double),
+                ("dfreq", ctypes.c_double), ("phi_left", ctypes.c_double), ("phi_right", ctypes.c_double),
+                ("f_left", ctypes.c_double), ("f_right", ctypes.c_double), ("total_phase", ctypes.c_double),
+                ("int_doppler", ctypes.c_double), ("interval_phase", ctypes.c_double)]
+
+
+def _track_protos(lib):
+    if getattr(lib, "_track_protos", False):
+        return
+    vp = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.pt_track_create.argtypes = [vp, ctypes.POINTER(TrackConfig), dp, ctypes.POINTER(vp)]
+    lib.pt_track_create.restype = ctypes.c_int
+    lib.pt_track_block.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(TrackResult)]
+    lib.pt_track_block.restype = ctypes.c_int
+    lib.pt_track_destroy.argtypes = [vp]
+    lib.pt_track_destroy.restype = None
+    lib._track_protos = True
+
+
+class Tracker:
+    """``pt_track``: block-to-block tracking of one stream on ``ctx`` (Sec. 3.1.4):
+    warm-started ranges, the Eq. 3-1-2 continuity check, enlarge-and-retry up to
+    ``max_attempts`` searches, and total phase / integration Doppler (Eq. 4-1-2).
+    ``block`` returns a dict of the ``pt_track_result`` fields."""
+
+    def __init__(self, ctx: Context, bounds, pop: int = 64, gens: int = 1250, F: float = 0.7, CR: float = 0.9,
+                 seed: int = 0, tier: int = TIER_F64, max_dphi: float = 0.3, max_dfreq: float = 2 * np.pi * 1.0,
+                 enlarge: float = 2.0, max_attempts: int = 3, count_interval: float = 0.0):
+        self._ctx = ctx
+        self._lib = ctx._lib
+        _track_protos(self._lib)
+        c = TrackConfig(int(pop), int(gens), float(F), float(CR), int(seed), int(tier), float(max_dphi),
+                        float(max_dfreq), float(enlarge), int(max_attempts), float(count_interval))
+        b = _dvec(bounds, 10)
+        h = ctypes.c_void_p()
+        ctx._check(self._lib.pt_track_create(ctx.handle, ctypes.byref(c), b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             ctypes.byref(h)))
+        self._h = h
+
+    def block(self, samples, fs: float, scale: float = 1.0) -> dict:
+        s = np.ascontiguousarray(samples)
+        r = TrackResult()
+        self._ctx._check(self._lib.pt_track_block(self._h, s.ctypes.data, s.size, _NP_TO_PT[s.dtype], float(scale),
+                                                  float(fs), ctypes.byref(r)))
+        out = {k: getattr(r, k) for k, _ in TrackResult._fields_}
+        out["params"] = np.array(list(r.params))
+        return out
+
+    def close(self):
+        if self._h:
+            self._lib.pt_track_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

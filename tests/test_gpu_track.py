@@ -1,0 +1,140 @@
+"""GPU tests of block-to-block tracking (pt_track_*, Sec. 3.1.4 data process flow).
+
+* A clean stream: every block is accepted at the first search (quality 1),
+  the border phase/frequency and the Eq. 4-1-2 total phase match the oracle's
+  evaluation of Eq. 3-1-1 / 4-1-2 at the same parameters, and the integration
+  Doppler over a count interval matches the stream's true phase change.
+* A block of noise only is abandoned after max_attempts searches (quality 0);
+  the next block is accepted without an adjacent reference and the count
+  interval restarts.
+* A chirp-rate jump at a block border puts the truth outside the running-time
+  ranges (Sec. 3.1.1 notes extrapolation fails when the phase derivatives are
+  not monotonic); the enlarged second search recovers it (quality 2).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    build.build()
+    c = pt.Context(0)
+    yield c
+    c.close()
+
+
+def _stream():
+    sp = synth.make_streams(seed=2)[0]  # 10 kHz
+    sp.block_s = 1.0
+    sp.snr_db = 25.0
+    return sp
+
+
+def test_clean_stream_observables_and_integration_doppler(ctx):
+    import paper_1906_10598_b300 as pt
+    sp = _stream()
+    b0 = synth.stream_block(sp, 0)
+    nblk, per_interval = 6, 3
+    tr = pt.Tracker(ctx, b0.bounds, pop=32, gens=400, seed=1, max_dphi=0.3, max_dfreq=2 * math.pi * 1.0,
+                    count_interval=per_interval * b0.T)
+    res = []
+    for k in range(nblk):
+        b = synth.stream_block(sp, k)
+        r = tr.block(b.samples, b.fs, b.scale)
+        res.append(r)
+        assert r["block_index"] == k and r["quality"] == 1 and r["attempts"] == 1
+        assert abs(r["params"][2] - b.truth[2]) < 0.05
+        T = b.T
+        c = oracle.theta_to_c(r["params"])
+        assert math.isclose(r["total_phase"], oracle.c_total_phase(c, T), rel_tol=1e-12, abs_tol=1e-9)
+        for t, key in ((-T / 2, "left"), (T / 2, "right")):
+            assert math.isclose(r["f_" + key], oracle.c_freq(c, t), rel_tol=1e-12, abs_tol=1e-9)
+            d = math.remainder(r["phi_" + key] - oracle.c_phase(c, t), 2 * math.pi)
+            assert abs(d) < 1e-9
+        if k == 0:
+            assert math.isnan(r["dphi"])
+        else:
+            assert r["dphi"] <= 0.3 and r["dfreq"] <= 2 * math.pi
+    # count intervals end at blocks 2 and 5
+    for k, r in enumerate(res):
+        if (k + 1) % per_interval:
+            assert math.isnan(r["int_doppler"])
+            continue
+        n = int(round(sp.block_s * sp.fs))
+        t_s = (k + 1 - per_interval) * n / sp.fs - 0.5 / sp.fs
+        t_e = (k + 1) * n / sp.fs - 0.5 / sp.fs
+        true_phase = 2 * math.pi * float(synth.stream_phase_cycles(sp, np.array([t_e]))[0]
+                                         - synth.stream_phase_cycles(sp, np.array([t_s]))[0])
+        assert abs(r["interval_phase"] - true_phase) < 0.05, (r["interval_phase"], true_phase)
+        assert math.isclose(r["int_doppler"], r["interval_phase"] / (per_interval * n / sp.fs), rel_tol=1e-12)
+    tr.close()
+
+
+def test_noise_block_is_abandoned_and_tracking_resumes(ctx):
+    import paper_1906_10598_b300 as pt
+    sp = _stream()
+    b0 = synth.stream_block(sp, 0)
+    # tight thresholds (a clean block's border residuals are ~1e-3 rad): a fit to
+    # noise cannot pass them by chance
+    tr = pt.Tracker(ctx, b0.bounds, pop=32, gens=300, seed=3, max_dphi=0.05, max_dfreq=2 * math.pi * 0.2,
+                    max_attempts=3, count_interval=2 * b0.T)
+    r0 = tr.block(b0.samples, b0.fs, b0.scale)
+    assert r0["quality"] == 1
+    b1 = synth.stream_block(sp, 1)
+    noise = np.random.default_rng(7).normal(0.0, 1.0, b1.n)
+    r1 = tr.block(noise, b1.fs, 1.0)
+    assert r1["quality"] == 0 and r1["attempts"] == 3 and math.isnan(r1["total_phase"])
+    assert math.isnan(r1["int_doppler"])
+    b2 = synth.stream_block(sp, 2)
+    r2 = tr.block(b2.samples, b2.fs, b2.scale)
+    # no adjacent accepted block: accepted unchecked, ranges extrapolated over the gap
+    assert r2["quality"] == 1 and math.isnan(r2["dphi"])
+    assert abs(r2["params"][2] - b2.truth[2]) < 0.05
+    # the interval restarted with block 2: it completes at block 3
+    assert math.isnan(r2["int_doppler"])
+    b3 = synth.stream_block(sp, 3)
+    r3 = tr.block(b3.samples, b3.fs, b3.scale)
+    assert r3["quality"] == 1 and not math.isnan(r3["int_doppler"])
+    tr.close()
+
+
+def _kinked_blocks(fs=2000.0, T=1.0, f0=100.0, f1b=8.0, A=1.0, sigma=0.05, seed=0):
+    """Two contiguous blocks of a tone whose chirp rate jumps from 0 to f1b at
+    their shared border (phase and frequency continuous there)."""
+    n = int(round(T * fs))
+    rng = np.random.default_rng(seed)
+    t = np.arange(2 * n) / fs
+    tb = n / fs - 0.5 / fs  # border between the blocks, halfway between samples n-1 and n
+    cyc = f0 * t + np.where(t > tb, f1b * (t - tb) ** 2 / 2, 0.0) + 0.1
+    x = A * np.cos(2 * np.pi * cyc) + rng.normal(0.0, sigma, 2 * n)
+    tc1 = (n + (n - 1) / 2) / fs
+    truth1 = np.array([A, 0.0, f0 + f1b * (tc1 - tb), f1b, 0.0])
+    return x[:n], x[n:], truth1
+
+
+def test_chirp_jump_recovered_by_enlarged_ranges(ctx):
+    import paper_1906_10598_b300 as pt
+    fs, T = 2000.0, 1.0
+    x0, x1, truth1 = _kinked_blocks(fs=fs, T=T)
+    bounds0 = np.array([[0.8, 1.2], [-np.pi, np.pi], [99.0, 101.0], [-0.5, 0.5], [-0.2, 0.2]])
+    tr = pt.Tracker(ctx, bounds0, pop=64, gens=600, seed=5, max_dphi=0.3, max_dfreq=2 * math.pi * 1.0,
+                    enlarge=3.0, max_attempts=3)
+    r0 = tr.block(x0, fs)
+    assert r0["quality"] == 1 and abs(r0["params"][2] - 100.0) < 0.01
+    # the running-time f0 range of block 1 is about 100 +- 2 Hz; the truth is 104 Hz
+    wb = pt.warm_bounds(r0["params"], T, T)
+    assert not (wb[2, 0] <= truth1[2] <= wb[2, 1])
+    r1 = tr.block(x1, fs)
+    assert r1["quality"] == 2 and r1["attempts"] == 2
+    assert abs(r1["params"][2] - truth1[2]) < 0.05 and abs(r1["params"][3] - truth1[3]) < 0.5
+    assert r1["dphi"] <= 0.3
+    tr.close()
