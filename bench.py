@@ -460,6 +460,59 @@ def run_serve(args):
     return 0
 
 
+def run_track(args):
+    """One station stream (20 kHz, 2 s blocks, quartic phase plus Doppler
+    sinusoid, 25 dB) tracked block by block with pt_track (Sec. 3.1.4): warm
+    ranges, Eq. 3-1-2 acceptance, enlarge-and-retry, integration Doppler over
+    10 s count intervals (Eq. 4-1-2). Reports blocks/s, the real-time factor,
+    the quality histogram and the integration-Doppler error against the
+    stream's true phase change."""
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    build.build()
+    sp = synth.make_streams(seed=11)[1]
+    sp.block_s, sp.snr_db = 2.0, 25.0
+    nblk, per_int = args.track_blocks, 5
+    blocks = [synth.stream_block(sp, k) for k in range(nblk)]
+    ctx = pt.Context(0)
+    tr = pt.Tracker(ctx, blocks[0].bounds, pop=64, gens=1250, seed=0, max_dphi=0.3,
+                    max_dfreq=2 * math.pi * 1.0, enlarge=2.0, max_attempts=3, count_interval=per_int * sp.block_s)
+    w = pt.Tracker(ctx, blocks[0].bounds, pop=64, gens=20)
+    w.block(blocks[0].samples, blocks[0].fs, blocks[0].scale)  # load the kernels
+    w.close()
+    t = time.perf_counter()
+    res = [tr.block(b.samples, b.fs, b.scale) for b in blocks]
+    wall = time.perf_counter() - t
+    q = [r["quality"] for r in res]
+    n = blocks[0].n
+    idop_err, dphi = [], [r["dphi"] for r in res if not math.isnan(r["dphi"])]
+    for k, r in enumerate(res):
+        if not math.isnan(r["int_doppler"]):
+            t_s = (k + 1 - per_int) * n / sp.fs - 0.5 / sp.fs
+            t_e = (k + 1) * n / sp.fs - 0.5 / sp.fs
+            true = 2 * math.pi * float(synth.stream_phase_cycles(sp, np.array([t_e]))[0]
+                                       - synth.stream_phase_cycles(sp, np.array([t_s]))[0]) / (t_e - t_s)
+            idop_err.append(abs(r["int_doppler"] - true))
+    f0err = [abs(r["params"][2] - b.truth[2]) for r, b in zip(res, blocks) if r["quality"] > 0]
+    line = {"metric": "tracked blocks/s", "value": nblk / wall, "unit": "blocks/s", "n_gpus": 1, "steps": nblk,
+            "warmup": 1, "ms_per_step": wall / nblk * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "track1_stream_20khz_2s", "fs": sp.fs, "block_s": sp.block_s, "blocks": nblk,
+                       "pop": 64, "gens": 1250, "count_interval_s": per_int * sp.block_s, "max_attempts": 3},
+            "real_time_factor": sp.block_s * nblk / wall,
+            "quality_histogram": {str(v): q.count(v) for v in sorted(set(q))},
+            "continuity_dphi_rad": {"median": float(np.median(dphi)) if dphi else None,
+                                    "max": float(np.max(dphi)) if dphi else None},
+            "f0_abs_err_hz_median": float(np.median(f0err)),
+            "int_doppler_abs_err_rad_s": {"intervals": len(idop_err),
+                                          "median": float(np.median(idop_err)) if idop_err else None,
+                                          "max": float(np.max(idop_err)) if idop_err else None}}
+    print(json.dumps(line))
+    tr.close()
+    ctx.close()
+    return 0
+
+
 def run_precision(args):
     """Precision sweep on the 400K block: samples stored as int8 / FP16 / FP32,
     phase evaluated by the FP64-anchored default tier, the double-float FP32
@@ -524,9 +577,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "precision"],
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "precision", "track"],
                     help="single: the 400K-block fit (default); batch: 256 uneven blocks in one launch; "
-                         "serve: 4 station streams through pt_submit/pt_poll")
+                         "serve: 4 station streams through pt_submit/pt_poll; track: one stream through pt_track")
+    ap.add_argument("--track-blocks", type=int, default=60, help="track: blocks of the tracked stream")
     ap.add_argument("--nblocks", type=int, default=256)
     ap.add_argument("--speedup", type=float, default=20.0, help="serve: real-time compression factor")
     ap.add_argument("--sim-seconds", type=float, default=120.0, help="serve: simulated stream duration")
@@ -541,6 +595,8 @@ def main():
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "track":
+        return run_track(args)
     if args.mode == "precision":
         return run_precision(args)
     return run_gpu(args)
