@@ -73,6 +73,17 @@ def _load():
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                           ctypes.c_uint32, dp, dp, dp, ctypes.c_int]
         lib.oc_de_solve_block.restype = ctypes.c_int
+        lib.oc_de_solve_block_obj.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                              ctypes.c_uint32, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+        lib.oc_de_solve_block_obj.restype = ctypes.c_int
+        for name in ("oc_cor", "oc_cor_objective"):
+            fn = getattr(lib, name)
+            fn.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp]
+            fn.restype = ctypes.c_double
+        lib.oc_cor_objective_many.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp,
+                                              ctypes.c_int64, dp, ctypes.c_int]
+        lib.oc_cor_objective_many.restype = None
         lib.oc_de_textbook.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_uint64, dp]
         lib.oc_de_textbook.restype = ctypes.c_int
@@ -132,18 +143,47 @@ def sse_many(samples, fs: float, t0: float, cands, nthreads: int = 0) -> np.ndar
     return out
 
 
+def cor(samples, fs: float, t0: float, theta) -> float:
+    """Eq. 2-2-5's cor: the unnormalised cross-correlation sum_i s_i m(t_i)."""
+    s = _f64(samples)
+    th = _f64(theta)
+    return _load().oc_cor(_dptr(s), s.size, float(fs), float(t0), _dptr(th))
+
+
+def cor_objective(samples, fs: float, t0: float, theta) -> float:
+    """Eq. 2-2-5 objective 1 / (atan(cor) + pi/2) of one candidate."""
+    s = _f64(samples)
+    th = _f64(theta)
+    return _load().oc_cor_objective(_dptr(s), s.size, float(fs), float(t0), _dptr(th))
+
+
+def cor_objective_many(samples, fs: float, t0: float, cands, nthreads: int = 0) -> np.ndarray:
+    s = _f64(samples)
+    c = _f64(cands).reshape(-1, D)
+    out = np.zeros(c.shape[0], dtype=np.float64)
+    _load().oc_cor_objective_many(_dptr(s), s.size, float(fs), float(t0), _dptr(c), c.shape[0], _dptr(out),
+                                  int(nthreads))
+    return out
+
+
+OBJECTIVES = {"chi2": 0, "cor": 1}
+
+
 def de_solve(samples, fs: float, t0: float, bounds, pop: int, gens: int, F: float, CR: float, seed: int,
-             block_id: int = 0, nthreads: int = 0, return_population: bool = False):
-    """DE/rand/1/bin fit of one block. Returns (params[5], sse) or, with
-    ``return_population``, (params, sse, population[pop,5], fitness[pop])."""
+             block_id: int = 0, nthreads: int = 0, return_population: bool = False, objective: str = "chi2"):
+    """DE/rand/1/bin fit of one block on the chi-square (Eq. 2-2-4) or the
+    correlation (Eq. 2-2-5) objective. Returns (params[5], objective value)
+    or, with ``return_population``, (params, value, population[pop,5],
+    fitness[pop])."""
     s = _f64(samples)
     b = _f64(bounds).reshape(D, 2)
     out = np.zeros(D + 1, dtype=np.float64)
     popv = np.zeros((pop, D), dtype=np.float64)
     fit = np.zeros(pop, dtype=np.float64)
-    rc = _load().oc_de_solve_block(_dptr(s), s.size, float(fs), float(t0), _dptr(b), int(pop), int(gens), float(F),
-                                   float(CR), ctypes.c_uint64(int(seed)), ctypes.c_uint32(int(block_id)), _dptr(out),
-                                   _dptr(popv), _dptr(fit), int(nthreads))
+    rc = _load().oc_de_solve_block_obj(_dptr(s), s.size, float(fs), float(t0), _dptr(b), int(pop), int(gens),
+                                       float(F), float(CR), ctypes.c_uint64(int(seed)),
+                                       ctypes.c_uint32(int(block_id)), int(OBJECTIVES[objective]), _dptr(out),
+                                       _dptr(popv), _dptr(fit), int(nthreads))
     if rc != 0:
         raise ValueError("oracle de_solve: invalid arguments")
     if return_population:

@@ -13,6 +13,13 @@
  *     i.e. c0 = phi0, c1 = 2 pi f0, c2 = pi f1, c3 = pi f2 / 3, c4 = A.
  *   - Chi-square objective with unit weights, Sec. 2.2 Eq. 2-2-4:
  *       F(theta) = sum_i (s_i - m(t_i))^2.
+ *   - Correlation objective, Sec. 2.2 Eq. 2-2-5 with the constant-amplitude
+ *     model of Eq. 2-2-6:
+ *       cor(theta) = sum_i s_i m(t_i),  F_cor(theta) = 1 / (atan(cor) + pi/2).
+ *     "cor" is read as the unnormalised cross-correlation: the paper states
+ *     F_cor converges to 1/pi, which a normalised coefficient (at most 1)
+ *     cannot reach; A is held constant by the caller (the paper's "average
+ *     amplitude"), since a fitted A makes F_cor divergent.
  *   - Differential Evolution, Sec. 1.2 (mutation -> crossover -> selection,
  *     Fig. "DE algorithm iteration flowchart") with the controls of Sec. 3.1.2
  *     Table 3-1-1 (F, CR, fixed itermax as the stop rule).  The mutation
@@ -113,6 +120,30 @@ double oc_sse(const double* s, int64_t n, double fs, double t0, const double th[
     acc += (long double)res * (long double)res;
   }
   return (double)acc;
+}
+
+/* Eq. 2-2-5 / 2-2-6: the unnormalised cross-correlation of the samples with
+ * the model (long double, index order) and the correlation objective. */
+double oc_cor(const double* s, int64_t n, double fs, double t0, const double th[OC_D]) {
+  long double acc = 0.0L;
+  for (int64_t i = 0; i < n; ++i) {
+    double t = t0 + (double)i / fs;
+    acc += (long double)s[i] * (long double)oc_model(th, t);
+  }
+  return (double)acc;
+}
+
+double oc_cor_objective(const double* s, int64_t n, double fs, double t0, const double th[OC_D]) {
+  return 1.0 / (atan(oc_cor(s, n, fs, t0, th)) + OC_PI / 2.0);
+}
+
+void oc_cor_objective_many(const double* s, int64_t n, double fs, double t0, const double* cands, int64_t ncand,
+                           double* out, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int64_t c = 0; c < ncand; ++c) out[c] = oc_cor_objective(s, n, fs, t0, cands + OC_D * c);
 }
 
 /* SSE for `ncand` candidate rows (row-major, 5 per row). */
@@ -251,13 +282,26 @@ static double oc_block_objective(const double* th, void* user) {
   return oc_sse(b->s, b->n, b->fs, b->t0, th);
 }
 
+static double oc_block_cor_objective(const double* th, void* user) {
+  const oc_block* b = (const oc_block*)user;
+  return oc_cor_objective(b->s, b->n, b->fs, b->t0, th);
+}
+
+/* objective 0: chi-square (Eq. 2-2-4); 1: correlation (Eq. 2-2-5). */
+int oc_de_solve_block_obj(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_D], int np,
+                          int gens, double F, double CR, uint64_t seed, uint32_t block_id, int objective,
+                          double out[OC_D + 1], double* final_pop, double* final_fit, int nthreads) {
+  if (n < 1 || !(fs > 0.0) || objective < 0 || objective > 1) return -1;
+  oc_block b = {s, n, fs, t0};
+  return oc_de_run(objective ? oc_block_cor_objective : oc_block_objective, &b, bounds, np, gens, F, CR, seed,
+                   block_id, out, final_pop, final_fit, nthreads);
+}
+
 int oc_de_solve_block(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_D], int np,
                       int gens, double F, double CR, uint64_t seed, uint32_t block_id, double out[OC_D + 1],
                       double* final_pop, double* final_fit, int nthreads) {
-  if (n < 1 || !(fs > 0.0)) return -1;
-  oc_block b = {s, n, fs, t0};
-  return oc_de_run(oc_block_objective, &b, bounds, np, gens, F, CR, seed, block_id, out, final_pop, final_fit,
-                   nthreads);
+  return oc_de_solve_block_obj(s, n, fs, t0, bounds, np, gens, F, CR, seed, block_id, 0, out, final_pop, final_fit,
+                               nthreads);
 }
 
 /* Textbook DE test functions (5-D), for the DE self-check. */

@@ -175,6 +175,103 @@ def test_sse_tiny_block_high_precision():
 
 
 # --------------------------------------------------------------------------
+# Correlation objective (Eq. 2-2-5 with the constant-amplitude model, Eq. 2-2-6)
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_cor_full_cycle_tone_closed_form(case):
+    # s = A0 cos(2 pi f t + ph) over a whole number of cycles, with 2 f not a
+    # multiple of fs: sum cos^2 = N/2, so cor at the truth with amplitude A is
+    # A A0 N / 2 and F_cor = 1 / (atan(A A0 N / 2) + pi/2)
+    rng = np.random.default_rng(300 + case)
+    n = int(rng.integers(50, 4000))
+    fs = float(rng.uniform(100, 20000))
+    k = int(rng.integers(1, n // 3))
+    f = k * fs / n
+    t0 = 0.0
+    a0, ph, a = rng.uniform(0.5, 2), rng.uniform(-3, 3), rng.uniform(0.1, 3)
+    s = a0 * np.cos(2 * np.pi * f * np.arange(n) / fs + ph)
+    th = [a, ph, f, 0.0, 0.0]
+    want = a * a0 * n / 2
+    assert oracle.cor(s, fs, t0, th) == pytest.approx(want, rel=1e-11, abs=1e-9)
+    assert oracle.cor_objective(s, fs, t0, th) == pytest.approx(1.0 / (math.atan(want) + math.pi / 2), rel=1e-12)
+    # a candidate j/T away in frequency is orthogonal: cor = 0, F_cor = 2/pi
+    j = int(rng.integers(1, 5))
+    off = [a, ph, f + j * fs / n, 0.0, 0.0]
+    assert abs(oracle.cor(s, fs, t0, off)) < 1e-9 * n
+    assert oracle.cor_objective(s, fs, t0, off) == pytest.approx(2 / math.pi, rel=1e-9)
+
+
+def test_cor_phase_flip_identity_and_limit():
+    # cos(x + pi) = -cos(x) gives cor(theta + pi) = -cor(theta), hence
+    # 1/F(theta) + 1/F(theta + pi) = pi for any data; and F -> 1/pi as cor grows
+    blk = synth.paper400k(5, n=4096)
+    s = blk.values()
+    rng = np.random.default_rng(1)
+    lo, hi = blk.bounds[:, 0], blk.bounds[:, 1]
+    for _ in range(5):
+        th = lo + rng.random(5) * (hi - lo)
+        flip = th.copy()
+        flip[1] += math.pi
+        c1, c2 = oracle.cor(s, blk.fs, blk.t0, th), oracle.cor(s, blk.fs, blk.t0, flip)
+        assert c2 == pytest.approx(-c1, rel=1e-9, abs=1e-9 * blk.n)
+        f1 = oracle.cor_objective(s, blk.fs, blk.t0, th)
+        f2 = oracle.cor_objective(s, blk.fs, blk.t0, flip)
+        assert 1 / f1 + 1 / f2 == pytest.approx(math.pi, rel=1e-12)
+    tr = np.array(blk.truth)
+    vals = []
+    for scale in (1.0, 10.0, 100.0):
+        t = tr.copy()
+        t[0] *= scale
+        vals.append(oracle.cor_objective(s, blk.fs, blk.t0, t))
+    assert all(v > 1 / math.pi for v in vals) and vals[0] > vals[1] > vals[2]
+    assert vals[2] - 1 / math.pi < 1e-5
+
+
+def test_cor_tiny_block_high_precision_and_many():
+    mp = mpmath
+    mp.mp.dps = 40
+    rng = np.random.default_rng(6)
+    for n in range(1, 9):
+        fs, t0 = 37.0, -0.31
+        s = rng.normal(0, 1, n)
+        th = [1.3, -2.0, 5.2, 0.7, -0.4]
+        want = mp.mpf(0)
+        for i in range(n):
+            t = mp.mpf(t0) + mp.mpf(i) / mp.mpf(fs)
+            ph = mp.mpf(th[1]) + 2 * mp.pi * (mp.mpf(th[2]) * t + mp.mpf(th[3]) * t ** 2 / 2 + mp.mpf(th[4]) * t ** 3 / 6)
+            want += mp.mpf(s[i]) * mp.mpf(th[0]) * mp.cos(ph)
+        assert oracle.cor(s, fs, t0, th) == pytest.approx(float(want), rel=1e-12, abs=1e-14)
+        assert oracle.cor_objective(s, fs, t0, th) == pytest.approx(float(1 / (mp.atan(want) + mp.pi / 2)), rel=1e-13)
+    blk = synth.paper400k(7, n=1000)
+    cands = blk.bounds[:, 0] + rng.random((9, 5)) * (blk.bounds[:, 1] - blk.bounds[:, 0])
+    many = oracle.cor_objective_many(blk.values(), blk.fs, blk.t0, cands, nthreads=3)
+    for c, v in zip(cands, many):
+        assert v == oracle.cor_objective(blk.values(), blk.fs, blk.t0, c)
+
+
+def test_de_on_cor_objective_finds_the_chi2_basin():
+    # With A held constant (lo = hi), minimising F_cor maximises the
+    # cross-correlation: on a tiny block it reaches the same (phi0, f0, f1)
+    # basin as the chi-square fit, and no point of a dense grid beats it.
+    rng = np.random.default_rng(0)
+    fs, n = 100.0, 64
+    t0 = synth.centred_t0(n, fs)
+    truth = np.array([1.0, 0.7, 3.1, 0.4, 0.0])
+    s = synth.clean_tone(truth, n, fs, t0) + rng.normal(0, 0.1, n)
+    bounds = np.array([[1.0, 1.0], [-np.pi, np.pi], [2.9, 3.3], [-1.0, 1.5], [-0.5, 0.5]])
+    x, f = oracle.de_solve(s, fs, t0, bounds, 40, 400, 0.7, 0.9, 5, objective="cor")
+    assert x[0] == 1.0
+    assert f == oracle.cor_objective(s, fs, t0, x)
+    grid = [[1.0, ph, f0, f1, 0.0] for ph in np.linspace(-np.pi, np.pi, 41)
+            for f0 in np.linspace(2.9, 3.3, 41) for f1 in np.linspace(-1.0, 1.5, 21)]
+    gvals = oracle.cor_objective_many(s, fs, t0, np.array(grid))
+    assert f <= gvals.min() + 1e-12
+    xc, _ = oracle.de_solve(s, fs, t0, bounds, 40, 400, 0.7, 0.9, 5)
+    assert abs(x[2] - xc[2]) < 0.02 and abs(np.angle(np.exp(1j * (x[1] - xc[1])))) < 0.2
+
+
+# --------------------------------------------------------------------------
 # Differential Evolution (Sec. 1.2, Table 3-1-1)
 
 
