@@ -200,7 +200,11 @@ def run_gpu(args):
     ctx.set_stream(stream.cuda_stream)
     ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2
-    bounds = blk.bounds
+    bounds = blk.bounds.copy()
+    if args.objective == "cor":
+        # Eq. 2-2-5 / 2-2-6: the amplitude is the constant average amplitude
+        ctx.set_objective("cor")
+        bounds[0] = (blk.truth[0], blk.truth[0])
     evals = blk.sample_evals()
 
     def step():
@@ -259,6 +263,8 @@ def run_gpu(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": blk.n, "fs": blk.fs, "storage": "int16", "pop": blk.pop,
                        "gens": blk.gens, "tier": "f64-anchored phase, f32 cos", "l2": "flushed between steps",
+                       "objective": "chi-square (Eq. 2-2-4)" if args.objective == "chi2" else
+                       "correlation (Eq. 2-2-5, constant A)",
                        "de_seconds": total_ms / args.steps * 1e-3, "wall_s": wall},
             "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(blk.samples.nbytes),
@@ -581,6 +587,8 @@ def main():
                     help="single: the 400K-block fit (default); batch: 256 uneven blocks in one launch; "
                          "serve: 4 station streams through pt_submit/pt_poll; track: one stream through pt_track")
     ap.add_argument("--track-blocks", type=int, default=60, help="track: blocks of the tracked stream")
+    ap.add_argument("--objective", default="chi2", choices=["chi2", "cor"],
+                    help="single: the objective minimised (cor: Eq. 2-2-5 with A held at the block's amplitude)")
     ap.add_argument("--nblocks", type=int, default=256)
     ap.add_argument("--speedup", type=float, default=20.0, help="serve: real-time compression factor")
     ap.add_argument("--sim-seconds", type=float, default=120.0, help="serve: simulated stream duration")

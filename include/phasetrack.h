@@ -82,6 +82,19 @@ typedef struct pt_ctx pt_ctx;
 #define PT_TIER_DF32 2
 #define PT_TIER_F32 3
 
+/* Objectives (Sec. 2.2), chosen per context with pt_set_objective:
+ *   PT_OBJ_CHI2  Eq. 2-2-4 with unit weights, sum_i (s_i - m(t_i))^2 (default);
+ *   PT_OBJ_COR   Eq. 2-2-5 with the constant-amplitude model of Eq. 2-2-6,
+ *                1 / (atan(cor) + pi/2), cor = sum_i s_i A cos(phi(t_i)), the
+ *                unnormalised cross-correlation (the reading under which the
+ *                objective tends to 1/pi at the fit, as the paper states).
+ *                A is each candidate's amplitude; a DE fit on PT_OBJ_COR
+ *                should hold it constant (bounds lo = hi = the average
+ *                amplitude), since a free A makes the objective divergent.
+ *                Default tier only. */
+#define PT_OBJ_CHI2 0
+#define PT_OBJ_COR 1
+
 /* Largest DE population supported by the device kernels. */
 #define PT_POP_MAX 128
 
@@ -112,6 +125,12 @@ PT_API void* pt_get_stream(const pt_ctx* ctx);
  *   fs       sampling rate in Hz (> 0); t_i = t0 + i / fs.
  * Replaces the context's current block. Errors: PT_EINVAL, PT_ENOMEM, PT_ECUDA. */
 PT_API int pt_load_block(pt_ctx* ctx, const void* samples, int64_t n, int dtype, double scale, double fs, double t0);
+
+/* Objective of the context's later pt_objective, pt_de_solve[_ex], pt_track
+ * and pt_batch calls (and of a serving loop configured afterwards): PT_OBJ_CHI2
+ * (default) or PT_OBJ_COR. Values returned as "sse" are then the objective
+ * value. Errors: PT_EINVAL. */
+PT_API int pt_set_objective(pt_ctx* ctx, int objective);
 
 /* Evaluate Eq. 2-2-4 for n candidates on the loaded block.
  *   cands    host or device pointer, n rows of 5 doubles (A, phi0, f0, f1, f2), row-major.

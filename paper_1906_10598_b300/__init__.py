@@ -24,6 +24,8 @@ PT_EINVAL, PT_ENOMEM, PT_EAGAIN, PT_ETIMEOUT, PT_ECUDA, PT_ENOTCONV, PT_ENOBLOCK
 PT_I8, PT_I16, PT_F16, PT_F32, PT_F64 = 0, 1, 2, 3, 4
 TIER_F64, TIER_PLAIN, TIER_DF32, TIER_F32 = 0, 1, 2, 3
 TIERS = {"f64": TIER_F64, "plain": TIER_PLAIN, "df32": TIER_DF32, "f32": TIER_F32}
+OBJ_CHI2, OBJ_COR = 0, 1
+OBJECTIVES = {"chi2": OBJ_CHI2, "cor": OBJ_COR}
 POP_MAX = 128
 
 _NP_TO_PT = {np.dtype(np.int8): PT_I8, np.dtype(np.int16): PT_I16, np.dtype(np.float16): PT_F16,
@@ -57,6 +59,8 @@ def load_library():
     lib.pt_last_error.restype = ctypes.c_char_p
     lib.pt_set_stream.argtypes = [vp, vp]
     lib.pt_set_stream.restype = c_int
+    lib.pt_set_objective.argtypes = [vp, c_int]
+    lib.pt_set_objective.restype = c_int
     lib.pt_get_stream.argtypes = [vp]
     lib.pt_get_stream.restype = vp
     lib.pt_load_block.argtypes = [vp, vp, i64, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -133,6 +137,10 @@ class Context:
 
     def set_stream(self, stream_handle: Optional[int]):
         self._check(self._lib.pt_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)))
+
+    def set_objective(self, objective):
+        """pt_set_objective: "chi2" (Eq. 2-2-4) or "cor" (Eq. 2-2-5), or OBJ_*."""
+        self._check(self._lib.pt_set_objective(self._h, int(OBJECTIVES.get(objective, objective))))
 
     def load_block(self, samples, fs: float, t0: float, scale: float = 1.0, dtype: Optional[int] = None):
         """pt_load_block: samples as numpy (host) or torch CUDA tensor (device)."""

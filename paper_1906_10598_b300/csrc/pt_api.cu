@@ -82,7 +82,7 @@ BlockArgs to_block_args(const HostBlock& h) {
 
 // ---- objective -------------------------------------------------------------
 
-template <int TIER, int CGV>
+template <int TIER, int CGV, int OBJ = OBJ_CHI2>
 int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
   ObjArgs a{};
   a.b = to_block_args(c->blk);
@@ -101,15 +101,22 @@ int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
   a.timeout_ns = c->timeout_ns;
   const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, a.b.esize, 0, NT);
   if (S.total > c->smem_optin) return fail(c, PT_EINVAL, "objective launch needs too much shared memory");
-  PT_CUDA(c, cudaFuncSetAttribute(k_objective<TIER, CGV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PT_CUDA(c, cudaFuncSetAttribute(k_objective<TIER, CGV, OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)S.total));
   dim3 grid(nx, ny);
-  k_objective<TIER, CGV><<<grid, NT, S.total, c->stream>>>(a);
+  k_objective<TIER, CGV, OBJ><<<grid, NT, S.total, c->stream>>>(a);
   PT_CUDA(c, cudaGetLastError());
   return PT_OK;
 }
 
 int launch_objective_any(pt_ctx* c, int tier, const double* d_cands, int ncand) {
+  if (c->objective == PT_OBJ_COR) {
+    if (tier != PT_TIER_F64) return fail(c, PT_EINVAL, "the correlation objective runs in the default tier only");
+    const int cg = pick_cg(tier, std::min(ncand, NP_MAX));
+    if (cg == 16) return launch_objective<TIER_F64, 16, OBJ_COR>(c, d_cands, ncand);
+    if (cg == 8) return launch_objective<TIER_F64, 8, OBJ_COR>(c, d_cands, ncand);
+    return launch_objective<TIER_F64, 4, OBJ_COR>(c, d_cands, ncand);
+  }
   switch (tier) {
     case PT_TIER_F64: {
       const int cg = pick_cg(tier, std::min(ncand, NP_MAX));
@@ -129,17 +136,17 @@ size_t smem_de(int tier, int sc_tiles, int esize_max) {
   return smem_layout(tier, NP_MAX, sc_tiles, 16, esize_max, NP_MAX, NT).total;
 }
 
-template <int TIER>
+template <int TIER, int OBJ = OBJ_CHI2>
 int launch_de_t(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
   const size_t smem = smem_de(TIER, a.sc_tiles, a.esize_max);
   if (smem > c->smem_optin) return fail(c, PT_EINVAL, "DE launch needs too much shared memory");
-  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER>, NT, smem));
+  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, OBJ>, NT, smem));
   const int grid = a.ngroups * a.k;
   if (occ < 1 || grid > occ * c->sms) return fail(c, PT_EINVAL, "DE grid cannot be co-resident");
   void* args[] = {&a};
-  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER>, dim3(grid), dim3(NT), args, smem, s));
+  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, OBJ>, dim3(grid), dim3(NT), args, smem, s));
   return PT_OK;
 }
 
@@ -266,6 +273,11 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   if (!(mode & DE_LAUNCH)) return PT_OK;
   PT_CUDA(c, cudaMemsetAsync(ring, 0, (size_t)ngroups * RING_GROUP_WORDS * sizeof(unsigned long long), s));
   PT_CUDA(c, cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  a.obj = c->objective;
+  if (a.obj == OBJ_COR) {
+    if (tier != PT_TIER_F64) return fail(c, PT_EINVAL, "the correlation objective runs in the default tier only");
+    return launch_de_t<TIER_F64, OBJ_COR>(c, s, a);
+  }
   switch (tier) {
     case PT_TIER_F64: return launch_de_t<TIER_F64>(c, s, a);
     case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN>(c, s, a);
@@ -353,6 +365,13 @@ void pt_destroy(pt_ctx* c) {
 
 const char* pt_last_error(const pt_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+int pt_set_objective(pt_ctx* c, int objective) {
+  if (!c) return PT_EINVAL;
+  if (objective != PT_OBJ_CHI2 && objective != PT_OBJ_COR) return fail(c, PT_EINVAL, "unknown objective");
+  c->objective = objective;
+  return PT_OK;
+}
+
 int pt_set_stream(pt_ctx* c, void* stream) {
   if (!c) return PT_EINVAL;
   c->stream = stream ? (cudaStream_t)stream : c->own_stream;
@@ -402,7 +421,7 @@ int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int
   rc = launch_objective_any(c, tier, d_c, (int)n);
   if (rc != PT_OK) return rc;
   k_finalize<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(d_c, (int)n, c->d_acc, c->blk.n, (float)c->blk.smax,
-                                                             d_out);
+                                                             d_out, c->objective);
   PT_CUDA(c, cudaGetLastError());
   PT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   if (!dev_out)

@@ -336,6 +336,41 @@ __device__ __forceinline__ double fixed_to_double(unsigned long long acc, int k)
 
 __device__ __forceinline__ float exp2_int_f(int k) { return __int_as_float((k + 127) << 23); }
 
+// Objectives (Sec. 2.2): the chi-square of Eq. 2-2-4 and the correlation
+// objective of Eq. 2-2-5 with the constant-amplitude model of Eq. 2-2-6,
+//   cor = sum_i s_i A cos(phi_i),  F_cor = 1 / (atan(cor) + pi/2),
+// "cor" read as the unnormalised cross-correlation (the paper's F_cor tends
+// to 1/pi at the fit, which a normalised coefficient cannot reach).
+constexpr int OBJ_CHI2 = 0;
+constexpr int OBJ_COR = 1;
+
+// Fixed-point exponent of a candidate's sum S = sum_i s_i cos(phi_i), signed:
+// |S| <= n smax = B, and k is chosen so that B 2^k < 2^(bits+1) (bits is one
+// less than for the unsigned chi-square sums, for the sign).
+constexpr int COR_BITS_OBJ = 59;
+constexpr int COR_BITS_DE = 52;
+__device__ __forceinline__ int cor_scale_exp(int64_t n, float smax, int bits) {
+  float B = (float)n * smax;
+  if (!(B > 1e-30f)) B = 1e-30f;
+  const int e = (int)((__float_as_uint(B) >> 23) & 0xff) - 126;  // B in [2^(e-1), 2^e)
+  int k = bits - e;
+  if (k > 120) k = 120;
+  if (k < -120) k = -120;
+  return k;
+}
+
+// A signed fixed-point sum acc * 2^-k as a double (|acc| < 2^62, |k| <= 120).
+__device__ __forceinline__ double signed_fixed_to_double(long long acc, int k) {
+  if (acc == 0) return 0.0;
+  const double v = (double)acc;
+  return __longlong_as_double(__double_as_longlong(v) - ((long long)k << 52));
+}
+
+// Eq. 2-2-5 from the candidate's amplitude and its sum S = sum_i s_i cos(phi_i).
+__device__ __forceinline__ double cor_objective_value(double A, double S) {
+  return 1.0 / (atan(A * S) + 1.5707963267948966192);
+}
+
 // ---------------------------------------------------------------------------
 // Warp reduce-scatter of N per-lane values (N a power of two <= 32): returns
 // the full-warp sum of value index lane / (32 / N); the 32 / N consecutive

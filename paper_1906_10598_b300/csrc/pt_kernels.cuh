@@ -106,7 +106,7 @@ __device__ __forceinline__ void prep_zero(unsigned char* cdata, float* negA, int
 // over separate threads so the 1/64-rate FP64 work is spread across all
 // warps of the CTA, and flags in cub[c] the candidates whose cubic term must
 // stay exact (cubic_needed). Ends with __syncthreads().
-template <int TIER>
+template <int TIER, int OBJ = OBJ_CHI2>
 __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs& b, unsigned char* cdata,
                          float* negA, int* kexp, unsigned char* cub, int kbits) {
   if (TIER == TIER_F64) {
@@ -119,7 +119,7 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
       } else if (c < nc) {
         const float Af = __double2float_rn(cands[c * D]);
         negA[c] = -Af;
-        kexp[c] = sse_scale_exp(b.n, b.smax_f, fabsf(Af), kbits);
+        kexp[c] = OBJ == OBJ_COR ? cor_scale_exp(b.n, b.smax_f, kbits) : sse_scale_exp(b.n, b.smax_f, fabsf(Af), kbits);
       } else {
         negA[c] = 0.f;
         kexp[c] = 0;
@@ -145,7 +145,8 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
 // so x = xc + m' Vc + m'^2 S2 + m'^3 E3 with xc = 2 pi frac(U0 + kc V) + S0
 // and Vc = 2 pi V + S1: three FFMAs per sample (none at the centre). MASKED
 // zeroes the residuals of samples at or past nvalid (the ragged last tile).
-template <bool MASKED>
+// OBJ_COR accumulates s_i cos(phi_i) instead of the squared residual.
+template <bool MASKED, int OBJ>
 __device__ __forceinline__ float cand_exact(const float (&s)[M], uint4 a, float nA, int lane, int nvalid) {
   const int kci = lane * M + M / 2;
   const float kc = (float)kci, kc2 = kc * kc;
@@ -162,9 +163,14 @@ __device__ __forceinline__ float cand_exact(const float (&s)[M], uint4 a, float 
     const float mp = (float)(m - M / 2);
     const float x = (m == M / 2) ? xc : fmaf(mp, Vc, fmaf(mp * mp, S2, fmaf(mp * mp * mp, E3, xc)));
     const float cv = __cosf(x);
-    float r = fmaf(nA, cv, s[m]);
-    if (MASKED) r = (lane * M + m < nvalid) ? r : 0.f;
-    sum = fmaf(r, r, sum);
+    if (OBJ == OBJ_COR) {
+      // samples past nvalid are the zero padding of the staged tile
+      sum = fmaf(s[m], cv, sum);
+    } else {
+      float r = fmaf(nA, cv, s[m]);
+      if (MASKED) r = (lane * M + m < nvalid) ? r : 0.f;
+      sum = fmaf(r, r, sum);
+    }
   }
   return sum;
 }
@@ -176,6 +182,7 @@ __device__ __forceinline__ float cand_exact(const float (&s)[M], uint4 a, float 
 //   Vc = 2 pi V + 2 kc E2c,     E2c = E2 + kc E3,
 // two FFMAs with constant m' per sample instead of the fixed-point walk
 // (none at the centre itself). |x| stays below (1 + M) pi.
+template <int OBJ>
 __device__ __forceinline__ float cand_fold(const float (&s)[M], uint4 a, float nA, int lane) {
   const int kci = lane * M + M / 2;
   const float kc = (float)kci;
@@ -190,8 +197,12 @@ __device__ __forceinline__ float cand_fold(const float (&s)[M], uint4 a, float n
     const float mp = (float)(m - M / 2);
     const float x = (m == M / 2) ? xc : fmaf(mp, Vc, fmaf(mp * mp, E2c, xc));
     const float cv = __cosf(x);
-    const float r = fmaf(nA, cv, s[m]);
-    sum = fmaf(r, r, sum);
+    if (OBJ == OBJ_COR) {
+      sum = fmaf(s[m], cv, sum);
+    } else {
+      const float r = fmaf(nA, cv, s[m]);
+      sum = fmaf(r, r, sum);
+    }
   }
   return sum;
 }
@@ -200,11 +211,11 @@ __device__ __forceinline__ float cand_fold(const float (&s)[M], uint4 a, float n
 // candidate and the tile: full tiles use cand_fold unless the candidate is
 // flagged (flags: its CGV bytes, nonzero = keep the exact cubic), the ragged
 // last tile always uses cand_exact.
-template <int CGV, bool MASKED>
+template <int CGV, bool MASKED, int OBJ>
 __device__ __forceinline__ void item_f64(const float (&s)[M], const uint4* anc_i, const float* negA_g, int lane,
                                          int nvalid, float (&acc)[CGV]) {
 #pragma unroll
-  for (int c = 0; c < CGV; ++c) acc[c] = cand_exact<MASKED>(s, anc_i[c], negA_g[c], lane, nvalid);
+  for (int c = 0; c < CGV; ++c) acc[c] = cand_exact<MASKED, OBJ>(s, anc_i[c], negA_g[c], lane, nvalid);
 }
 // The CGV values -A of an item's candidates (negA_g 16-byte aligned, CGV a
 // multiple of 4), in 16-byte loads.
@@ -219,21 +230,21 @@ __device__ __forceinline__ void load_negA(const float* negA_g, float (&nA)[CGV])
     nA[c + 3] = v.w;
   }
 }
-template <int CGV>
+template <int CGV, int OBJ>
 __device__ __forceinline__ void item_f64_fold(const float (&s)[M], const uint4* anc_i, const float* negA_g, int lane,
                                               float (&acc)[CGV]) {
   float nA[CGV];
-  load_negA<CGV>(negA_g, nA);
+  if (OBJ == OBJ_CHI2) load_negA<CGV>(negA_g, nA);
 #pragma unroll
-  for (int c = 0; c < CGV; ++c) acc[c] = cand_fold(s, anc_i[c], nA[c], lane);
+  for (int c = 0; c < CGV; ++c) acc[c] = cand_fold<OBJ>(s, anc_i[c], OBJ == OBJ_CHI2 ? nA[c] : 0.f, lane);
 }
-template <int CGV>
+template <int CGV, int OBJ>
 __device__ __forceinline__ void item_f64_mixed(const float (&s)[M], const uint4* anc_i, const float* negA_g,
                                                const unsigned char* flags, int lane, float (&acc)[CGV]) {
 #pragma unroll
   for (int c = 0; c < CGV; ++c) {
-    if (flags[c]) acc[c] = cand_exact<false>(s, anc_i[c], negA_g[c], lane, L);
-    else acc[c] = cand_fold(s, anc_i[c], negA_g[c], lane);
+    if (flags[c]) acc[c] = cand_exact<false, OBJ>(s, anc_i[c], negA_g[c], lane, L);
+    else acc[c] = cand_fold<OBJ>(s, anc_i[c], negA_g[c], lane);
   }
 }
 
@@ -364,7 +375,7 @@ __device__ __forceinline__ bool any_flag(const unsigned char* f) {
 // the default tier each warp computes the tile anchors of its next IPB items
 // itself into its own slice of `anc` (IPB * CGV entries per warp), so no
 // CTA-wide barrier separates anchors from evaluation. Ends with __syncthreads().
-template <int TIER, int CGV>
+template <int TIER, int CGV, int OBJ = OBJ_CHI2>
 __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, int item_hi, const float* s32,
                            const double* s64, const unsigned char* cdata, const float* negA, const int* kexp,
                            const unsigned char* cub, int ncand, int npad, uint4* anc, unsigned long long* acc) {
@@ -441,10 +452,10 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
         if (TIER == TIER_F64) {
           const uint4* anc_i = anc_w + k * CGV;
           if (nvalid == L) {
-            if (any_flag<CGV>(cub + g * CGV)) item_f64_mixed<CGV>(s, anc_i, nA, cub + g * CGV, lane, accv);
-            else item_f64_fold<CGV>(s, anc_i, nA, lane, accv);
+            if (any_flag<CGV>(cub + g * CGV)) item_f64_mixed<CGV, OBJ>(s, anc_i, nA, cub + g * CGV, lane, accv);
+            else item_f64_fold<CGV, OBJ>(s, anc_i, nA, lane, accv);
           } else {
-            item_f64<CGV, true>(s, anc_i, nA, lane, nvalid, accv);
+            item_f64<CGV, true, OBJ>(s, anc_i, nA, lane, nvalid, accv);
           }
         } else if (TIER == TIER_DF32) {
           if (nvalid == L) item_df32<CGV, false>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
@@ -547,7 +558,7 @@ struct ObjArgs {
   uint64_t timeout_ns;
 };
 
-template <int TIER, int CGV>
+template <int TIER, int CGV, int OBJ = OBJ_CHI2>
 __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int64_t tb = (int64_t)blockIdx.x * a.tpc;
@@ -570,18 +581,25 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
 
   const int tid = threadIdx.x;
   if (tid < npad) acc[tid] = 0ull;
-  prep_all<TIER>(a.cands + (int64_t)cb * D, nc, npad, a.b, cdata, negA, kexp, cub, SSE_BITS_OBJ);
+  prep_all<TIER, OBJ>(a.cands + (int64_t)cb * D, nc, npad, a.b, cdata, negA, kexp, cub,
+                      OBJ == OBJ_COR ? COR_BITS_OBJ : SSE_BITS_OBJ);
   if (!stage_tiles<TIER>(a.b, tb, nt, raw, s32, s64, mbar, a.timeout_ns, a.err)) return;
-  eval_range<TIER, CGV>(a.b, tb, 0, nt * (npad / CGV), s32, s64, cdata, negA, kexp, cub, nc, npad, anc, acc);
+  eval_range<TIER, CGV, OBJ>(a.b, tb, 0, nt * (npad / CGV), s32, s64, cdata, negA, kexp, cub, nc, npad, anc, acc);
   if (tid < nc) atomicAdd(&a.acc[cb + tid], acc[tid]);
 }
 
+// The objective value of each candidate from its fixed-point sum: the SSE,
+// or for OBJ_COR F_cor from S = sum s_i cos(phi_i) and the candidate's A.
 static __global__ void k_finalize(const double* cands, int ncand, const unsigned long long* acc, int64_t n, float smax_f,
-                           double* sse) {
+                                  double* sse, int obj) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncand) return;
-  const int k = sse_scale_exp(n, smax_f, fabsf(__double2float_rn(cands[(int64_t)c * D])), SSE_BITS_OBJ);
-  sse[c] = fixed_to_double(acc[c], k);
+  const double A = cands[(int64_t)c * D];
+  if (obj == OBJ_COR) {
+    sse[c] = cor_objective_value(A, signed_fixed_to_double((long long)acc[c], cor_scale_exp(n, smax_f, COR_BITS_OBJ)));
+  } else {
+    sse[c] = fixed_to_double(acc[c], sse_scale_exp(n, smax_f, fabsf(__double2float_rn(A)), SSE_BITS_OBJ));
+  }
 }
 
 // One block's DE problem (device-side descriptor).
@@ -607,6 +625,7 @@ struct DeLaunch {
   unsigned long long* ring;  // [ngroups][3][NP_MAX][RING_STRIDE], zeroed by the caller
   int* err;                  // zeroed by the caller
   uint64_t timeout_ns;
+  int obj;                   // OBJ_CHI2 or OBJ_COR (the kernel instantiation launched)
 };
 
 struct DeSmem {
@@ -633,7 +652,7 @@ struct DeSmem {
 // replaces a barrier, a fence and a separate read. `gg` counts the group's
 // generations across blocks so the ring discipline continues from block to
 // block. Returns false if a bounded wait expired or another CTA failed.
-template <int TIER, int CGV>
+template <int TIER, int CGV, int OBJ>
 __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long long* ring, unsigned long long& gg,
                          const DeSmem& sm, const DeLaunch& a, int* s_abort) {
   const int tid = threadIdx.x;
@@ -675,17 +694,18 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     }
     if (tid < npad) sm.acc[tid] = 0ull;
     __syncthreads();
-    prep_all<TIER>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub, SSE_BITS_DE);
+    prep_all<TIER, OBJ>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub,
+                        OBJ == OBJ_COR ? COR_BITS_DE : SSE_BITS_DE);
     if (resident) {
-      eval_range<TIER, CGV>(b, tb, ilo, ihi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad, sm.anc,
-                            sm.acc);
+      eval_range<TIER, CGV, OBJ>(b, tb, ilo, ihi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
+                                 sm.anc, sm.acc);
     } else {
       for (int c0 = 0; c0 < nt; c0 += a.sc_tiles) {
         const int cn = min(a.sc_tiles, nt - c0);
         const int lo = max(ilo, c0 * G) - c0 * G, hi = min(ihi, (c0 + cn) * G) - c0 * G;
         if (!stage_tiles<TIER>(b, tb + c0, cn, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err)) return false;
-        eval_range<TIER, CGV>(b, tb + c0, lo, hi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
-                              sm.anc, sm.acc);
+        eval_range<TIER, CGV, OBJ>(b, tb + c0, lo, hi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np,
+                                   npad, sm.anc, sm.acc);
       }
     }
     if (tid < np) {
@@ -715,9 +735,15 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
           }
         }
       }
-      const double f = fixed_to_double(v >> 8, sm.kexp[tid]);
-      // SSE values are non-negative: their bit patterns order like the values
-      if (gen == 0 || __double_as_longlong(f) <= __double_as_longlong(sm.fx[tid])) {
+      // the words' sums are signed for OBJ_COR (two's complement adds); the low
+      // byte counts arrivals either way
+      // OBJ_COR ranks by -cor (F_cor = 1/(atan(cor) + pi/2) decreases strictly
+      // with cor), so no FP64 arctangent sits on the generation's critical
+      // path; F_cor is formed once for the outputs. dkey orders signed doubles.
+      const double f = OBJ == OBJ_COR
+                           ? -(sm.u[tid * D] * signed_fixed_to_double((long long)v >> 8, sm.kexp[tid]))
+                           : fixed_to_double(v >> 8, sm.kexp[tid]);
+      if (gen == 0 || dkey(f) <= dkey(sm.fx[tid])) {
         sm.fx[tid] = f;
 #pragma unroll
         for (int j = 0; j < D; ++j) sm.x[tid * D + j] = sm.u[tid * D + j];
@@ -734,22 +760,24 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     if (tid == 0) {
       int best = 0;
       for (int i = 1; i < np; ++i)
-        if (__double_as_longlong(sm.fx[i]) < __double_as_longlong(sm.fx[best])) best = i;
+        if (dkey(sm.fx[i]) < dkey(sm.fx[best])) best = i;
       for (int j = 0; j < D; ++j) d.out[j] = sm.x[best * D + j];
-      d.out[D] = sm.fx[best];
+      d.out[D] = OBJ == OBJ_COR ? cor_objective_value(1.0, -sm.fx[best]) : sm.fx[best];
     }
     if (d.pop_out)
       for (int i = tid; i < np * D; i += blockDim.x) d.pop_out[i] = sm.x[i];
     if (d.fit_out)
-      for (int i = tid; i < np; i += blockDim.x) d.fit_out[i] = sm.fx[i];
+      for (int i = tid; i < np; i += blockDim.x)
+        d.fit_out[i] = OBJ == OBJ_COR ? cor_objective_value(1.0, -sm.fx[i]) : sm.fx[i];
   }
   __syncthreads();
   return true;
 }
 
 // Persistent DE launch over groups of blocks (one block: one group of all CTAs).
-// Launched cooperatively: the k CTAs of a group wait on one another.
-template <int TIER>
+// Launched cooperatively: the k CTAs of a group wait on one another. OBJ
+// selects the objective every block of the launch minimises.
+template <int TIER, int OBJ = OBJ_CHI2>
 __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const SmemLayout S = smem_layout(TIER, NP_MAX, a.sc_tiles, 16, a.esize_max, NP_MAX, NT);
@@ -784,9 +812,9 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
     __syncthreads();
     const DeBlockDesc& d = s_desc;
     bool ok;
-    if (TIER == TIER_F64 && d.cg == 16) ok = de_block<TIER, 16>(d, rank, a.k, ring, gg, sm, a, &s_abort);
-    else if (TIER == TIER_F64 && d.cg == 4) ok = de_block<TIER, 4>(d, rank, a.k, ring, gg, sm, a, &s_abort);
-    else ok = de_block<TIER, 8>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    if (TIER == TIER_F64 && d.cg == 16) ok = de_block<TIER, 16, OBJ>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    else if (TIER == TIER_F64 && d.cg == 4) ok = de_block<TIER, 4, OBJ>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    else ok = de_block<TIER, 8, OBJ>(d, rank, a.k, ring, gg, sm, a, &s_abort);
     if (!ok) return;
   }
 }
