@@ -75,7 +75,10 @@ def _load():
         lib.oc_de_solve_block.restype = ctypes.c_int
         lib.oc_de_solve_block_obj.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
-                                              ctypes.c_uint32, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+                                              ctypes.c_uint32, ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+        lib.oc_de_textbook_strategy.argtypes = [ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_uint64, ctypes.c_int, dp]
+        lib.oc_de_textbook_strategy.restype = ctypes.c_int
         lib.oc_de_solve_block_obj.restype = ctypes.c_int
         for name in ("oc_cor", "oc_cor_objective"):
             fn = getattr(lib, name)
@@ -167,10 +170,13 @@ def cor_objective_many(samples, fs: float, t0: float, cands, nthreads: int = 0) 
 
 
 OBJECTIVES = {"chi2": 0, "cor": 1}
+# DE strategies: the default rand/1/bin, and the paper's "3" and "6" (Table 3-1-1)
+STRATEGIES = {"rand1bin": 0, "best1jitter": 3, "eitheror": 6}
 
 
 def de_solve(samples, fs: float, t0: float, bounds, pop: int, gens: int, F: float, CR: float, seed: int,
-             block_id: int = 0, nthreads: int = 0, return_population: bool = False, objective: str = "chi2"):
+             block_id: int = 0, nthreads: int = 0, return_population: bool = False, objective: str = "chi2",
+             strategy: str = "rand1bin"):
     """DE/rand/1/bin fit of one block on the chi-square (Eq. 2-2-4) or the
     correlation (Eq. 2-2-5) objective. Returns (params[5], objective value)
     or, with ``return_population``, (params, value, population[pop,5],
@@ -182,7 +188,8 @@ def de_solve(samples, fs: float, t0: float, bounds, pop: int, gens: int, F: floa
     fit = np.zeros(pop, dtype=np.float64)
     rc = _load().oc_de_solve_block_obj(_dptr(s), s.size, float(fs), float(t0), _dptr(b), int(pop), int(gens),
                                        float(F), float(CR), ctypes.c_uint64(int(seed)),
-                                       ctypes.c_uint32(int(block_id)), int(OBJECTIVES[objective]), _dptr(out),
+                                       ctypes.c_uint32(int(block_id)), int(OBJECTIVES[objective]),
+                                       int(STRATEGIES[strategy]), _dptr(out),
                                        _dptr(popv), _dptr(fit), int(nthreads))
     if rc != 0:
         raise ValueError("oracle de_solve: invalid arguments")
@@ -191,12 +198,14 @@ def de_solve(samples, fs: float, t0: float, bounds, pop: int, gens: int, F: floa
     return out[:D].copy(), float(out[D])
 
 
-def de_textbook(which: str, bounds, pop: int, gens: int, F: float, CR: float, seed: int):
+def de_textbook(which: str, bounds, pop: int, gens: int, F: float, CR: float, seed: int,
+                strategy: str = "rand1bin"):
     """The oracle's DE on a 5-D textbook function ('sphere' or 'rosenbrock')."""
     b = _f64(bounds).reshape(D, 2)
     out = np.zeros(D + 1, dtype=np.float64)
-    rc = _load().oc_de_textbook(0 if which == "sphere" else 1, _dptr(b), int(pop), int(gens), float(F), float(CR),
-                                ctypes.c_uint64(int(seed)), _dptr(out))
+    rc = _load().oc_de_textbook_strategy(0 if which == "sphere" else 1, _dptr(b), int(pop), int(gens), float(F),
+                                         float(CR), ctypes.c_uint64(int(seed)), int(STRATEGIES[strategy]),
+                                         _dptr(out))
     if rc != 0:
         raise ValueError("oracle de_textbook: invalid arguments")
     return out[:D].copy(), float(out[D])

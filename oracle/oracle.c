@@ -23,8 +23,10 @@
  *   - Differential Evolution, Sec. 1.2 (mutation -> crossover -> selection,
  *     Fig. "DE algorithm iteration flowchart") with the controls of Sec. 3.1.2
  *     Table 3-1-1 (F, CR, fixed itermax as the stop rule).  The mutation
- *     strategy is DE/rand/1 with binomial crossover; the paper names its
- *     strategies only by number, so the textbook rand/1/bin form is used.
+ *     strategy is DE/rand/1 with binomial crossover by default; the paper
+ *     names its strategies only by number, and its "3" and "6" are read as
+ *     DE/best/1 with jitter and the DE/rand/1 either-or algorithm (see
+ *     oc_de_run_strategy).
  *   - Derived observables: phase and instantaneous frequency, Sec. 3.1.3
  *     Eq. 3-1-1; block total-count phase, Sec. 4.1.1 Eq. 4-1-2.
  *   - Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
@@ -201,13 +203,53 @@ static void oc_pick3(uint32_t i, uint32_t np, const uint32_t w[3], uint32_t r[3]
   }
 }
 
-/* Runs DE; returns 0 on success, -1 on invalid arguments.
+/* Mutation strategies. Table 3-1-1 names the strategy only by number
+ * ("3 | 6": the third for the chi-square, the sixth for the correlation
+ * objective, Sec. 3.1.2) and counts six, citing Price, Storn & Lampinen,
+ * "Differential Evolution: A Practical Approach to Global Optimization"
+ * (2006); the third and sixth are read in that book's order. With r1, r2,
+ * r3 the three drawn indices (all different from i and each other):
+ *   OC_DE_RAND1_BIN    v = x_r1 + F (x_r2 - x_r3), binomial crossover (the
+ *                      textbook default, used when no strategy is named);
+ *   OC_DE_BEST1_JITTER v_j = x_best,j + F_j (x_r2,j - x_r3,j) with the
+ *                      per-component jitter F_j = F + 1e-4 U_j (U_j uniform
+ *                      in [0,1)), binomial crossover; x_best is the
+ *                      lowest-index minimum of the previous generation;
+ *   OC_DE_EITHER_OR    with probability 1/2 the rand/1 mutant, otherwise the
+ *                      three-point recombination v = x_r1 + K ((x_r2 + x_r3)
+ *                      - 2 x_r1), K = (F + 1)/2; the trial is v itself (no
+ *                      crossover). */
+#define OC_DE_RAND1_BIN 0
+#define OC_DE_BEST1_JITTER 3
+#define OC_DE_EITHER_OR 6
+
+/* The jitter and either-or words of individual ind at generation gen: words
+ * 9..11 of the three-group draw, then a fourth counter group (word group 3). */
+static void oc_draw_extra(uint64_t seed, uint32_t block_id, uint32_t gen, uint32_t ind, uint32_t w4[4]) {
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t ctr[4] = {3u, ind, gen, block_id};
+  oc_philox4x32_10(ctr, key, w4);
+}
+
+int oc_de_run_strategy(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], int np, int gens, double F,
+                       double CR, uint64_t seed, uint32_t block_id, int strategy, double out[OC_D + 1],
+                       double* final_pop, double* final_fit, int nthreads);
+
+/* Runs DE/rand/1/bin; returns 0 on success, -1 on invalid arguments.
  * out[0..4] = best vector, out[5] = its objective value.
  * final_pop (np*5) and final_fit (np) are optional. */
 int oc_de_run(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], int np, int gens, double F,
               double CR, uint64_t seed, uint32_t block_id, double out[OC_D + 1], double* final_pop,
               double* final_fit, int nthreads) {
+  return oc_de_run_strategy(obj, user, bounds, np, gens, F, CR, seed, block_id, OC_DE_RAND1_BIN, out, final_pop,
+                            final_fit, nthreads);
+}
+
+int oc_de_run_strategy(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], int np, int gens, double F,
+                       double CR, uint64_t seed, uint32_t block_id, int strategy, double out[OC_D + 1],
+                       double* final_pop, double* final_fit, int nthreads) {
   if (np < 4 || gens < 0) return -1;
+  if (strategy != OC_DE_RAND1_BIN && strategy != OC_DE_BEST1_JITTER && strategy != OC_DE_EITHER_OR) return -1;
   double lo[OC_D], hi[OC_D];
   for (int j = 0; j < OC_D; ++j) {
     lo[j] = bounds[2 * j];
@@ -238,17 +280,37 @@ int oc_de_run(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], in
 
   uint32_t cr_thr = CR >= 1.0 ? 0xffffffffu : (uint32_t)(CR * 4294967296.0);
   int cr_all = CR >= 1.0;
+  const double K = (F + 1.0) * 0.5;
   for (int g = 1; g <= gens; ++g) {
+    /* the previous generation's best (lowest index on ties), for best/1 */
+    int best = 0;
+    for (int i = 1; i < np; ++i)
+      if (fx[i] < fx[best]) best = i;
     /* mutation + crossover for every individual, from the generation-(g-1) population */
     for (int i = 0; i < np; ++i) {
-      uint32_t w[12], r[3];
+      uint32_t w[12], r[3], w4[4];
       oc_draw12(seed, block_id, (uint32_t)g, (uint32_t)i, w);
       oc_pick3((uint32_t)i, (uint32_t)np, w, r);
       uint32_t jrand = oc_lemire(w[3], OC_D);
+      if (strategy == OC_DE_BEST1_JITTER) oc_draw_extra(seed, block_id, (uint32_t)g, (uint32_t)i, w4);
+      const int three_point = strategy == OC_DE_EITHER_OR && w[9] >= 0x80000000u;
       for (int j = 0; j < OC_D; ++j) {
         double parent = x[i * OC_D + j];
-        int take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
-        double v = x[r[0] * OC_D + j] + F * (x[r[1] * OC_D + j] - x[r[2] * OC_D + j]);
+        const double a = x[r[0] * OC_D + j], b = x[r[1] * OC_D + j], c = x[r[2] * OC_D + j];
+        double v;
+        int take;
+        if (strategy == OC_DE_BEST1_JITTER) {
+          const uint32_t jw = j < 3 ? w[9 + j] : w4[j - 3];
+          const double Fj = F + 1e-4 * ((double)jw * (1.0 / 4294967296.0));
+          v = x[best * OC_D + j] + Fj * (b - c);
+          take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
+        } else if (strategy == OC_DE_EITHER_OR) {
+          v = three_point ? a + K * ((b + c) - 2.0 * a) : a + F * (b - c);
+          take = 1;
+        } else {
+          v = a + F * (b - c);
+          take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
+        }
         u[i * OC_D + j] = take ? oc_repair(j, v, parent, lo, hi) : parent;
       }
     }
@@ -287,21 +349,22 @@ static double oc_block_cor_objective(const double* th, void* user) {
   return oc_cor_objective(b->s, b->n, b->fs, b->t0, th);
 }
 
-/* objective 0: chi-square (Eq. 2-2-4); 1: correlation (Eq. 2-2-5). */
+/* objective 0: chi-square (Eq. 2-2-4); 1: correlation (Eq. 2-2-5);
+ * strategy: OC_DE_RAND1_BIN, OC_DE_BEST1_JITTER or OC_DE_EITHER_OR. */
 int oc_de_solve_block_obj(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_D], int np,
                           int gens, double F, double CR, uint64_t seed, uint32_t block_id, int objective,
-                          double out[OC_D + 1], double* final_pop, double* final_fit, int nthreads) {
+                          int strategy, double out[OC_D + 1], double* final_pop, double* final_fit, int nthreads) {
   if (n < 1 || !(fs > 0.0) || objective < 0 || objective > 1) return -1;
   oc_block b = {s, n, fs, t0};
-  return oc_de_run(objective ? oc_block_cor_objective : oc_block_objective, &b, bounds, np, gens, F, CR, seed,
-                   block_id, out, final_pop, final_fit, nthreads);
+  return oc_de_run_strategy(objective ? oc_block_cor_objective : oc_block_objective, &b, bounds, np, gens, F, CR,
+                            seed, block_id, strategy, out, final_pop, final_fit, nthreads);
 }
 
 int oc_de_solve_block(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_D], int np,
                       int gens, double F, double CR, uint64_t seed, uint32_t block_id, double out[OC_D + 1],
                       double* final_pop, double* final_fit, int nthreads) {
-  return oc_de_solve_block_obj(s, n, fs, t0, bounds, np, gens, F, CR, seed, block_id, 0, out, final_pop, final_fit,
-                               nthreads);
+  return oc_de_solve_block_obj(s, n, fs, t0, bounds, np, gens, F, CR, seed, block_id, 0, OC_DE_RAND1_BIN, out,
+                               final_pop, final_fit, nthreads);
 }
 
 /* Textbook DE test functions (5-D), for the DE self-check. */
@@ -325,6 +388,12 @@ int oc_de_textbook(int which, const double bounds[2 * OC_D], int np, int gens, d
                    double out[OC_D + 1]) {
   oc_objective_fn f = which == 0 ? oc_sphere : oc_rosenbrock;
   return oc_de_run(f, NULL, bounds, np, gens, F, CR, seed, 0u, out, NULL, NULL, 1);
+}
+
+int oc_de_textbook_strategy(int which, const double bounds[2 * OC_D], int np, int gens, double F, double CR,
+                            uint64_t seed, int strategy, double out[OC_D + 1]) {
+  oc_objective_fn f = which == 0 ? oc_sphere : oc_rosenbrock;
+  return oc_de_run_strategy(f, NULL, bounds, np, gens, F, CR, seed, 0u, strategy, out, NULL, NULL, 1);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -289,6 +289,58 @@ def test_de_textbook_rosenbrock_converges():
     assert np.allclose(x, 1.0, atol=1e-2)
 
 
+@pytest.mark.parametrize("strategy", ["rand1bin", "best1jitter", "eitheror"])
+def test_de_strategies_converge_on_sphere(strategy):
+    b = np.array([[-5.0, 5.0]] * 5)
+    x, f = oracle.de_textbook("sphere", b, pop=30, gens=800, F=0.5, CR=0.9, seed=1, strategy=strategy)
+    assert f < 1e-12 and np.all(np.abs(x) < 1e-6)
+
+
+def _rosenbrock_grad(x):
+    g = np.zeros_like(x)
+    for j in range(len(x) - 1):
+        a = x[j + 1] - x[j] ** 2
+        g[j] += -400.0 * x[j] * a - 2.0 * (1.0 - x[j])
+        g[j + 1] += 200.0 * a
+    return g
+
+
+def test_de_either_or_solves_rosenbrock():
+    b = np.array([[-2.0, 2.0]] * 5)
+    x, f = oracle.de_textbook("rosenbrock", b, pop=40, gens=8000, F=0.8, CR=0.9, seed=3, strategy="eitheror")
+    assert f < 1e-12 and np.allclose(x, 1.0, atol=1e-6)
+
+
+def test_de_best1_jitter_reaches_a_stationary_point():
+    # the greedy best/1 settles on the 5-D Rosenbrock function's other local
+    # minimum (x1 ~ -0.96); whichever minimum it reports, the gradient there
+    # must vanish (an independent check of the search, not of its formula)
+    b = np.array([[-2.0, 2.0]] * 5)
+    x, f = oracle.de_textbook("rosenbrock", b, pop=40, gens=4000, F=0.5, CR=0.9, seed=0, strategy="best1jitter")
+    assert np.linalg.norm(_rosenbrock_grad(x)) < 1e-4
+    assert f < 1e-8 or 3.9 < f < 3.95
+
+
+@pytest.mark.parametrize("strategy,objective", [("best1jitter", "chi2"), ("eitheror", "cor")])
+def test_de_strategies_beat_brute_force_grid(strategy, objective):
+    # the paper's pairings (Sec. 3.1.2): "3" with Eq. 2-2-4, "6" with Eq. 2-2-5
+    rng = np.random.default_rng(0)
+    fs, n = 100.0, 64
+    t0 = synth.centred_t0(n, fs)
+    truth = np.array([1.0, 0.7, 3.1, 0.4, 0.0])
+    s = synth.clean_tone(truth, n, fs, t0) + rng.normal(0, 0.1, n)
+    bounds = np.array([[0.8, 1.2], [-np.pi, np.pi], [2.9, 3.3], [-1.0, 1.5], [-0.5, 0.5]])
+    if objective == "cor":
+        bounds[0] = (1.0, 1.0)
+    grid = np.array([[1.0, ph, f0, f1, 0.0] for ph in np.linspace(-np.pi, np.pi, 41)
+                     for f0 in np.linspace(2.9, 3.3, 41) for f1 in np.linspace(-1.0, 1.5, 21)])
+    gvals = (oracle.cor_objective_many if objective == "cor" else oracle.sse_many)(s, fs, t0, grid)
+    x, f = oracle.de_solve(s, fs, t0, bounds, 40, 400, 0.7, 0.9, 5, objective=objective, strategy=strategy)
+    assert f <= gvals.min() + 1e-9
+    g = grid[int(np.argmin(gvals))]
+    assert abs(x[2] - g[2]) < 0.02 and abs(np.angle(np.exp(1j * (x[1] - g[1])))) < 0.2
+
+
 def test_de_prefix_monotone_and_in_bounds():
     # Counter-based draws make a run of G generations a prefix of a run of
     # G + k generations: the best objective can only improve.
