@@ -95,6 +95,23 @@ typedef struct pt_ctx pt_ctx;
 #define PT_OBJ_CHI2 0
 #define PT_OBJ_COR 1
 
+/* DE mutation strategies, chosen per context with pt_set_strategy. Table
+ * 3-1-1 names the strategy by number only ("3" for Eq. 2-2-4, "6" for
+ * Eq. 2-2-5, Sec. 3.1.2), counting six; they are read in the order of
+ * Price, Storn & Lampinen (2006), which the paper cites. r1, r2, r3 are the
+ * drawn indices (distinct, different from i):
+ *   PT_DE_RAND1_BIN     v = x_r1 + F (x_r2 - x_r3), binomial crossover (default);
+ *   PT_DE_BEST1_JITTER  "3": v_j = x_best,j + F_j (x_r2,j - x_r3,j) with
+ *                       F_j = F + 1e-4 U_j per component, binomial crossover,
+ *                       x_best the previous generation's lowest-index minimum;
+ *   PT_DE_EITHER_OR     "6": with probability 1/2 the rand/1 mutant, otherwise
+ *                       x_r1 + K ((x_r2 + x_r3) - 2 x_r1), K = (F + 1)/2; the
+ *                       trial is the mutant itself (no crossover).
+ * Out-of-range components are repaired as for the default. */
+#define PT_DE_RAND1_BIN 0
+#define PT_DE_BEST1_JITTER 3
+#define PT_DE_EITHER_OR 6
+
 /* Largest DE population supported by the device kernels. */
 #define PT_POP_MAX 128
 
@@ -131,6 +148,11 @@ PT_API int pt_load_block(pt_ctx* ctx, const void* samples, int64_t n, int dtype,
  * (default) or PT_OBJ_COR. Values returned as "sse" are then the objective
  * value. Errors: PT_EINVAL. */
 PT_API int pt_set_objective(pt_ctx* ctx, int objective);
+
+/* DE strategy of the context's later pt_de_solve[_ex], pt_track and
+ * pt_batch calls: PT_DE_RAND1_BIN (default), PT_DE_BEST1_JITTER or
+ * PT_DE_EITHER_OR. Errors: PT_EINVAL. */
+PT_API int pt_set_strategy(pt_ctx* ctx, int strategy);
 
 /* Evaluate Eq. 2-2-4 for n candidates on the loaded block.
  *   cands    host or device pointer, n rows of 5 doubles (A, phi0, f0, f1, f2), row-major.

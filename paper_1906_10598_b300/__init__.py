@@ -26,6 +26,8 @@ TIER_F64, TIER_PLAIN, TIER_DF32, TIER_F32 = 0, 1, 2, 3
 TIERS = {"f64": TIER_F64, "plain": TIER_PLAIN, "df32": TIER_DF32, "f32": TIER_F32}
 OBJ_CHI2, OBJ_COR = 0, 1
 OBJECTIVES = {"chi2": OBJ_CHI2, "cor": OBJ_COR}
+DE_RAND1_BIN, DE_BEST1_JITTER, DE_EITHER_OR = 0, 3, 6
+STRATEGIES = {"rand1bin": DE_RAND1_BIN, "best1jitter": DE_BEST1_JITTER, "eitheror": DE_EITHER_OR}
 POP_MAX = 128
 
 _NP_TO_PT = {np.dtype(np.int8): PT_I8, np.dtype(np.int16): PT_I16, np.dtype(np.float16): PT_F16,
@@ -61,6 +63,8 @@ def load_library():
     lib.pt_set_stream.restype = c_int
     lib.pt_set_objective.argtypes = [vp, c_int]
     lib.pt_set_objective.restype = c_int
+    lib.pt_set_strategy.argtypes = [vp, c_int]
+    lib.pt_set_strategy.restype = c_int
     lib.pt_get_stream.argtypes = [vp]
     lib.pt_get_stream.restype = vp
     lib.pt_load_block.argtypes = [vp, vp, i64, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -137,6 +141,10 @@ class Context:
 
     def set_stream(self, stream_handle: Optional[int]):
         self._check(self._lib.pt_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)))
+
+    def set_strategy(self, strategy):
+        """pt_set_strategy: "rand1bin" (default), "best1jitter" ("3") or "eitheror" ("6"), or DE_*."""
+        self._check(self._lib.pt_set_strategy(self._h, int(STRATEGIES.get(strategy, strategy))))
 
     def set_objective(self, objective):
         """pt_set_objective: "chi2" (Eq. 2-2-4) or "cor" (Eq. 2-2-5), or OBJ_*."""

@@ -139,7 +139,9 @@ size_t smem_de(int tier, int sc_tiles, int esize_max) {
 template <int TIER, int OBJ = OBJ_CHI2>
 int launch_de_t(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
   const size_t smem = smem_de(TIER, a.sc_tiles, a.esize_max);
-  if (smem > c->smem_optin) return fail(c, PT_EINVAL, "DE launch needs too much shared memory");
+  cudaFuncAttributes fa{};
+  PT_CUDA(c, cudaFuncGetAttributes(&fa, k_de<TIER, OBJ>));
+  if (smem + fa.sharedSizeBytes > c->smem_optin) return fail(c, PT_EINVAL, "DE launch needs too much shared memory");
   PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, OBJ>, NT, smem));
@@ -158,9 +160,13 @@ size_t o_off(int nblocks) { return o_sched(nblocks) + align_up((size_t)nblocks *
 
 size_t de_desc_bytes(int nblocks, int ngroups) { return o_off(nblocks) + (size_t)(ngroups + 1) * sizeof(int); }
 
+// The DE kernel's static shared memory (its block descriptor and a few flags,
+// under 1 KB) comes out of the same per-block opt-in budget as the dynamic part.
+constexpr size_t DE_STATIC_SMEM_RESERVE = 2048;
+
 int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want) {
   int sc = (int)std::max<int64_t>(1, std::min<int64_t>(want, 96));
-  while (sc > 1 && smem_de(tier, sc, esize_max) > c->smem_optin) sc--;
+  while (sc > 1 && smem_de(tier, sc, esize_max) + DE_STATIC_SMEM_RESERVE > c->smem_optin) sc--;
   return sc;
 }
 
@@ -237,6 +243,8 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
       d.dc.hi[j] = h.hi[j];
     }
     d.dc.F = h.F;
+    d.dc.K = (h.F + 1.0) * 0.5;
+    d.dc.strategy = c->strategy;
     d.dc.cr_all = h.CR >= 1.0;
     d.dc.cr_thr = h.CR >= 1.0 ? 0xffffffffu : (uint32_t)(h.CR * 4294967296.0);
     d.dc.periodic = (h.hi[1] - h.lo[1]) >= 2.0 * 3.14159265358979323846 * (1.0 - 1e-12);
@@ -364,6 +372,14 @@ void pt_destroy(pt_ctx* c) {
 }
 
 const char* pt_last_error(const pt_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int pt_set_strategy(pt_ctx* c, int strategy) {
+  if (!c) return PT_EINVAL;
+  if (strategy != PT_DE_RAND1_BIN && strategy != PT_DE_BEST1_JITTER && strategy != PT_DE_EITHER_OR)
+    return fail(c, PT_EINVAL, "unknown DE strategy");
+  c->strategy = strategy;
+  return PT_OK;
+}
 
 int pt_set_objective(pt_ctx* c, int objective) {
   if (!c) return PT_EINVAL;

@@ -119,12 +119,27 @@ __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
 }
 
 // DE controls shared by the kernels.
+// Mutation strategies (Table 3-1-1 names them by number: "3" for the
+// chi-square, "6" for the correlation objective, Sec. 3.1.2; read in the
+// order of Price, Storn & Lampinen 2006, which the paper cites):
+//   DE_RAND1_BIN     v = x_r1 + F (x_r2 - x_r3), binomial crossover (default);
+//   DE_BEST1_JITTER  v_j = x_best,j + F_j (x_r2,j - x_r3,j), F_j = F + 1e-4 U_j,
+//                    binomial crossover, x_best the previous generation's
+//                    lowest-index minimum;
+//   DE_EITHER_OR     with probability 1/2 the rand/1 mutant, otherwise
+//                    x_r1 + K ((x_r2 + x_r3) - 2 x_r1), K = (F + 1)/2; no crossover.
+constexpr int DE_RAND1_BIN = 0;
+constexpr int DE_BEST1_JITTER = 3;
+constexpr int DE_EITHER_OR = 6;
+
 struct DeControls {
   double lo[D], hi[D];
   double F;
+  double K;          // (F + 1) / 2, for DE_EITHER_OR
   uint32_t cr_thr;   // crossover if word < cr_thr
   int cr_all;        // CR >= 1
   int periodic;      // phi0 range spans the full circle
+  int strategy;      // DE_*
   uint2 key;         // Philox key (seed lo, seed hi)
   uint32_t block_id;
 };
@@ -148,10 +163,21 @@ __device__ __forceinline__ long long dkey(double a) {
 // Random draws of individual i at generation gen >= 1 (selection-independent):
 // r1, r2, r3 packed in bytes 0..2 (distinct, != i), crossover mask in `take`
 // (bit j set = component j comes from the mutant).
+// DE_EITHER_OR marks a three-point trial in bit 24 of rpack and takes every
+// component; DE_BEST1_JITTER also writes the five jitter words of the trial
+// (words 9..11, then words 0..1 of a fourth counter group) to jit[0..4].
 __device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, uint32_t gen, uint32_t* rpack,
-                                         uint32_t* take) {
+                                         uint32_t* take, uint32_t* jit) {
   uint32_t w[12];
   de_draw12(dc.key, dc.block_id, gen, (uint32_t)i, w);
+  if (dc.strategy == DE_BEST1_JITTER) {
+    const uint4 g3 = philox4x32_10(make_uint4(3u, (uint32_t)i, gen, dc.block_id), dc.key);
+    jit[0] = w[9];
+    jit[1] = w[10];
+    jit[2] = w[11];
+    jit[3] = g3.x;
+    jit[4] = g3.y;
+  }
   // three distinct indices != i, by index shifting over the sorted exclusions
   uint32_t excl[4];
   uint32_t r[3];
@@ -177,6 +203,10 @@ __device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, ui
     if ((uint32_t)j == jrand || dc.cr_all || w[4 + j] < dc.cr_thr) m |= 1u << j;
   *rpack = r[0] | (r[1] << 8) | (r[2] << 16);
   *take = m;
+  if (dc.strategy == DE_EITHER_OR) {
+    *take = (1u << D) - 1u;
+    if (w[9] >= 0x80000000u) *rpack |= 1u << 24;
+  }
 }
 
 // x * 0.5, exactly as the FP64 multiply would round it: when x is normal and
@@ -191,12 +221,27 @@ __device__ __forceinline__ double half_exact(double x) {
 // Component j of the DE/rand/1/bin trial of individual i from population x
 // (np x 5). FP64 operations use _rn intrinsics so no contraction changes a
 // rounding: the value is bit-identical to a plain IEEE evaluation.
+// STRAT is the DE_* strategy (a template parameter, so each strategy's loop
+// holds only its own FP64 operations); `best` (the previous generation's
+// lowest-index minimum) and jit (the trial's five jitter words) are used by
+// DE_BEST1_JITTER only.
+template <int STRAT>
 __device__ __forceinline__ double de_component(const DeControls& dc, const double* x, int i, int j, uint32_t rpack,
-                                               uint32_t take) {
+                                               uint32_t take, int best, const uint32_t* jit) {
   const double parent = x[i * D + j];
   if (!((take >> j) & 1u)) return parent;
   const int r0 = rpack & 0xff, r1 = (rpack >> 8) & 0xff, r2 = (rpack >> 16) & 0xff;
-  double v = __dadd_rn(x[r0 * D + j], __dmul_rn(dc.F, __dsub_rn(x[r1 * D + j], x[r2 * D + j])));
+  double v;
+  if (STRAT == DE_BEST1_JITTER) {
+    const double Fj = __dadd_rn(dc.F, __dmul_rn(1e-4, (double)jit[j] * (1.0 / 4294967296.0)));
+    v = __dadd_rn(x[best * D + j], __dmul_rn(Fj, __dsub_rn(x[r1 * D + j], x[r2 * D + j])));
+  } else if (STRAT == DE_EITHER_OR) {
+    const double a = x[r0 * D + j], b = x[r1 * D + j], c = x[r2 * D + j];
+    if (rpack >> 24) v = __dadd_rn(a, __dmul_rn(dc.K, __dsub_rn(__dadd_rn(b, c), 2.0 * a)));
+    else v = __dadd_rn(a, __dmul_rn(dc.F, __dsub_rn(b, c)));
+  } else {
+    v = __dadd_rn(x[r0 * D + j], __dmul_rn(dc.F, __dsub_rn(x[r1 * D + j], x[r2 * D + j])));
+  }
   if (j == 1 && dc.periodic) {
     const double d = __dsub_rn(v, dc.lo[j]);
     // k = floor(fl(d / 2pi)) without dividing: for d in [-4pi, 5pi) the

@@ -84,6 +84,7 @@ struct pt_ctx {
   float last_ms = 0.f;
   uint64_t timeout_ns = 2000000000ull;
   int objective = 0;  // PT_OBJ_CHI2 or PT_OBJ_COR, for pt_objective and the DE entry points
+  int strategy = 0;   // PT_DE_*, for the DE entry points
   // autotune cache of the batched launcher: per-CTA rate and per-generation costs
   double tune_rate = 0.0, tune_fixed_s = 0.0;
   double tune_rate_stream = 0.0;  // per-CTA rate when a CTA's tiles are staged chunk by chunk

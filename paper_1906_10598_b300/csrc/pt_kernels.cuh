@@ -526,7 +526,7 @@ __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, 
   s.off_acc = o;
   o += align_up((size_t)npad * sizeof(unsigned long long), 16);
   s.off_draw = o;
-  o += align_up((size_t)(pop ? 2 * npad : 0) * sizeof(uint32_t), 16);
+  o += align_up((size_t)(pop ? 7 * npad : 0) * sizeof(uint32_t), 16);  // rpack, take, 5 jitter words
   s.off_anc = o;
   o += (tier == TIER_F64) ? (size_t)(nthreads / 32) * IPB * cgv * sizeof(uint4) : 0;
   s.off_samp = o;
@@ -630,18 +630,28 @@ struct DeLaunch {
 
 struct DeSmem {
   uint64_t* mbar;
+  int* best;  // the previous generation's best individual (DE_BEST1_JITTER)
   double *x, *u, *fx;
   unsigned char* cdata;
   float* negA;
   int* kexp;
   unsigned char* cub;
   unsigned long long* acc;
-  uint32_t *drp, *drt;
+  uint32_t *drp, *drt, *drj;  // packed indices, crossover mask, 5 jitter words per individual
   uint4* anc;
   float* s32;
   double* s64;
   void* raw;
 };
+
+// Every trial component of the generation, one thread per (individual, component).
+template <int STRAT>
+__device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& sm, int np, int npad) {
+  for (int t = threadIdx.x; t < D * npad; t += blockDim.x) {
+    const int j = t / npad, c = t - j * npad;
+    if (c < np) sm.u[c * D + j] = de_component<STRAT>(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c], *sm.best, sm.drj + c * D);
+  }
+}
 
 // DE/rand/1/bin on one block by `k` CTAs (this one is `rank`). Every CTA holds
 // the whole population and generates every trial itself (identical Philox
@@ -683,14 +693,38 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
       ring[((gg + 1) % 3) * (NP_MAX * RING_STRIDE) + tid * RING_STRIDE] = 0ull;
       __threadfence();
     }
+    // DE_BEST1_JITTER mutates from the previous generation's lowest-index
+    // minimum: one warp's argmin over the selected fitnesses
+    if (d.dc.strategy == DE_BEST1_JITTER && gen > 0) {
+      if (tid < 32) {
+        int bi = -1;
+        long long bk = 0;
+        for (int i = tid; i < np; i += 32) {
+          const long long ki = dkey(sm.fx[i]);
+          if (bi < 0 || ki < bk) {
+            bi = i;
+            bk = ki;
+          }
+        }
+        for (int o = 16; o; o >>= 1) {
+          const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (oi >= 0 && (bi < 0 || ok < bk || (ok == bk && oi < bi))) {
+            bi = oi;
+            bk = ok;
+          }
+        }
+        if (tid == 0) *sm.best = bi;
+      }
+      __syncthreads();
+    }
     // trials u of this generation (the initial population at gen 0)
     if (gen == 0) {
       if (tid < np) de_init(d.dc, tid, sm.u + tid * D);
     } else {
-      for (int t = tid; t < D * npad; t += blockDim.x) {
-        const int j = t / npad, c = t - j * npad;
-        if (c < np) sm.u[c * D + j] = de_component(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c]);
-      }
+      if (d.dc.strategy == DE_BEST1_JITTER) mutate_all<DE_BEST1_JITTER>(d, sm, np, npad);
+      else if (d.dc.strategy == DE_EITHER_OR) mutate_all<DE_EITHER_OR>(d, sm, np, npad);
+      else mutate_all<DE_RAND1_BIN>(d, sm, np, npad);
     }
     if (tid < npad) sm.acc[tid] = 0ull;
     __syncthreads();
@@ -751,7 +785,7 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     } else if (gen < d.gens && tid >= NP_MAX && tid < NP_MAX + np) {
       // the next generation's draws do not depend on selection: overlap them with the wait
       const int c = tid - NP_MAX;
-      de_draws(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c]);
+      de_draws(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
     }
     __syncthreads();
     if (*s_abort) return false;
@@ -793,12 +827,18 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
   sm.acc = reinterpret_cast<unsigned long long*>(smem + S.off_acc);
   sm.drp = reinterpret_cast<uint32_t*>(smem + S.off_draw);
   sm.drt = sm.drp + NP_MAX;
+  sm.drj = sm.drp + 2 * NP_MAX;
   sm.anc = reinterpret_cast<uint4*>(smem + S.off_anc);
   sm.s32 = reinterpret_cast<float*>(smem + S.off_samp);
   sm.s64 = reinterpret_cast<double*>(smem + S.off_samp);
   sm.raw = smem + S.off_raw;
   __shared__ int s_abort;
-  if (threadIdx.x == 0) s_abort = 0;
+  __shared__ int s_best;
+  sm.best = &s_best;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_best = 0;
+  }
   __syncthreads();
 
   const int q = blockIdx.x / a.k, rank = blockIdx.x - q * a.k;

@@ -1,0 +1,93 @@
+"""GPU parity of the DE strategies "3" (DE/best/1 with jitter) and "6" (the
+DE/rand/1 either-or algorithm) of Table 3-1-1 against the oracle.
+
+The draws and the FP64 trial arithmetic are the oracle's, so the populations
+agree bit for bit until a selection compares two objective values closer than
+the tier's error; the fits agree within the benchmark spec's tolerances.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    build.build()
+    c = pt.Context(0)
+    yield c
+    c.set_strategy("rand1bin")
+    c.set_objective("chi2")
+    c.close()
+
+
+CASES = [("best1jitter", "chi2", "plain"), ("eitheror", "chi2", "plain"), ("eitheror", "cor", "f64"),
+         ("best1jitter", "cor", "f64")]
+
+
+@pytest.mark.parametrize("strategy,objective,tier", CASES)
+def test_early_generations_bit_identical(ctx, strategy, objective, tier):
+    import paper_1906_10598_b300 as pt
+    blk = synth.single4096(3)
+    b = blk.bounds.copy()
+    if objective == "cor":
+        b[0] = (blk.truth[0], blk.truth[0])
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    ctx.set_strategy(strategy)
+    ctx.set_objective(objective)
+    try:
+        for gens, CR in ((1, 0.9), (6, 0.9), (6, 1.0)):
+            _, _, gpop, gfit = ctx.de_solve(b, 32, gens, 0.7, CR, 77, pt.TIERS[tier], return_population=True)
+            _, _, opop, ofit = oracle.de_solve(blk.values(), blk.fs, blk.t0, b, 32, gens, 0.7, CR, 77,
+                                               return_population=True, objective=objective, strategy=strategy)
+            same = np.all(gpop == opop, axis=1)
+            assert same.sum() >= 31, (gens, CR, np.where(~same))
+            if objective == "cor":
+                # compare the cross-correlations behind F_cor against their scale
+                # n smax A (F_cor's relative error follows cor's absolute error
+                # where cor is near 0)
+                cg, co = np.tan(1 / gfit[same] - np.pi / 2), np.tan(1 / ofit[same] - np.pi / 2)
+                scale = blk.n * float(np.max(np.abs(blk.values()))) * blk.truth[0]
+                assert np.all(np.abs(cg - co) <= 2e-6 * scale)
+            else:
+                tol = 1e-9 if tier == "plain" else 1e-6
+                assert np.all(np.abs(gfit[same] - ofit[same]) <= tol * ofit[same])
+    finally:
+        ctx.set_strategy("rand1bin")
+        ctx.set_objective("chi2")
+
+
+@pytest.mark.parametrize("strategy,objective", [("best1jitter", "chi2"), ("eitheror", "cor")])
+def test_strategy_fit_matches_oracle(ctx, strategy, objective):
+    # the paper's pairings (Sec. 3.1.2): "3" with Eq. 2-2-4, "6" with Eq. 2-2-5
+    import paper_1906_10598_b300 as pt
+    blk = synth.paper400k(4, n=20_000)
+    b = blk.bounds.copy()
+    if objective == "cor":
+        b[0] = (blk.truth[0], blk.truth[0])
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    ctx.set_strategy(strategy)
+    ctx.set_objective(objective)
+    try:
+        g, gf = ctx.de_solve(b, 32, 300, 0.7, 0.9, 21, pt.TIER_F64)
+        o, of = oracle.de_solve(blk.values(), blk.fs, blk.t0, b, 32, 300, 0.7, 0.9, 21, objective=objective,
+                                strategy=strategy)
+        assert abs(math.remainder(g[1] - o[1], 2 * math.pi)) < 1e-3 and abs(g[2] - o[2]) < 1e-5
+        want = (oracle.cor_objective if objective == "cor" else oracle.sse)(blk.values(), blk.fs, blk.t0, g)
+        assert gf == pytest.approx(want, rel=1e-6)
+    finally:
+        ctx.set_strategy("rand1bin")
+        ctx.set_objective("chi2")
+
+
+def test_strategy_invalid(ctx):
+    import paper_1906_10598_b300 as pt
+    with pytest.raises(pt.PhaseTrackError):
+        ctx.set_strategy(4)
