@@ -166,11 +166,12 @@ __device__ __forceinline__ long long dkey(double a) {
 // DE_EITHER_OR marks a three-point trial in bit 24 of rpack and takes every
 // component; DE_BEST1_JITTER also writes the five jitter words of the trial
 // (words 9..11, then words 0..1 of a fourth counter group) to jit[0..4].
+template <int STRAT>
 __device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, uint32_t gen, uint32_t* rpack,
                                          uint32_t* take, uint32_t* jit) {
   uint32_t w[12];
   de_draw12(dc.key, dc.block_id, gen, (uint32_t)i, w);
-  if (dc.strategy == DE_BEST1_JITTER) {
+  if (STRAT == DE_BEST1_JITTER) {
     const uint4 g3 = philox4x32_10(make_uint4(3u, (uint32_t)i, gen, dc.block_id), dc.key);
     jit[0] = w[9];
     jit[1] = w[10];
@@ -203,7 +204,7 @@ __device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, ui
     if ((uint32_t)j == jrand || dc.cr_all || w[4 + j] < dc.cr_thr) m |= 1u << j;
   *rpack = r[0] | (r[1] << 8) | (r[2] << 16);
   *take = m;
-  if (dc.strategy == DE_EITHER_OR) {
+  if (STRAT == DE_EITHER_OR) {
     *take = (1u << D) - 1u;
     if (w[9] >= 0x80000000u) *rpack |= 1u << 24;
   }

@@ -630,7 +630,6 @@ struct DeLaunch {
 
 struct DeSmem {
   uint64_t* mbar;
-  int* best;  // the previous generation's best individual (DE_BEST1_JITTER)
   double *x, *u, *fx;
   unsigned char* cdata;
   float* negA;
@@ -645,11 +644,25 @@ struct DeSmem {
 };
 
 // Every trial component of the generation, one thread per (individual, component).
+// DE_BEST1_JITTER mutates from the previous generation's lowest-index
+// minimum, which each thread finds itself (broadcast reads of the fitnesses,
+// no extra CTA barrier in the generation loop).
 template <int STRAT>
 __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& sm, int np, int npad) {
+  int best = 0;
+  if (STRAT == DE_BEST1_JITTER) {
+    long long bk = dkey(sm.fx[0]);
+    for (int i = 1; i < np; ++i) {
+      const long long ki = dkey(sm.fx[i]);
+      if (ki < bk) {
+        bk = ki;
+        best = i;
+      }
+    }
+  }
   for (int t = threadIdx.x; t < D * npad; t += blockDim.x) {
     const int j = t / npad, c = t - j * npad;
-    if (c < np) sm.u[c * D + j] = de_component<STRAT>(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c], *sm.best, sm.drj + c * D);
+    if (c < np) sm.u[c * D + j] = de_component<STRAT>(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c], best, sm.drj + c * D);
   }
 }
 
@@ -692,31 +705,6 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     if (rank == 0 && tid < NP_MAX) {
       ring[((gg + 1) % 3) * (NP_MAX * RING_STRIDE) + tid * RING_STRIDE] = 0ull;
       __threadfence();
-    }
-    // DE_BEST1_JITTER mutates from the previous generation's lowest-index
-    // minimum: one warp's argmin over the selected fitnesses
-    if (d.dc.strategy == DE_BEST1_JITTER && gen > 0) {
-      if (tid < 32) {
-        int bi = -1;
-        long long bk = 0;
-        for (int i = tid; i < np; i += 32) {
-          const long long ki = dkey(sm.fx[i]);
-          if (bi < 0 || ki < bk) {
-            bi = i;
-            bk = ki;
-          }
-        }
-        for (int o = 16; o; o >>= 1) {
-          const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (oi >= 0 && (bi < 0 || ok < bk || (ok == bk && oi < bi))) {
-            bi = oi;
-            bk = ok;
-          }
-        }
-        if (tid == 0) *sm.best = bi;
-      }
-      __syncthreads();
     }
     // trials u of this generation (the initial population at gen 0)
     if (gen == 0) {
@@ -785,7 +773,12 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     } else if (gen < d.gens && tid >= NP_MAX && tid < NP_MAX + np) {
       // the next generation's draws do not depend on selection: overlap them with the wait
       const int c = tid - NP_MAX;
-      de_draws(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
+      if (d.dc.strategy == DE_BEST1_JITTER)
+        de_draws<DE_BEST1_JITTER>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
+      else if (d.dc.strategy == DE_EITHER_OR)
+        de_draws<DE_EITHER_OR>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
+      else
+        de_draws<DE_RAND1_BIN>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
     }
     __syncthreads();
     if (*s_abort) return false;
@@ -833,12 +826,7 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
   sm.s64 = reinterpret_cast<double*>(smem + S.off_samp);
   sm.raw = smem + S.off_raw;
   __shared__ int s_abort;
-  __shared__ int s_best;
-  sm.best = &s_best;
-  if (threadIdx.x == 0) {
-    s_abort = 0;
-    s_best = 0;
-  }
+  if (threadIdx.x == 0) s_abort = 0;
   __syncthreads();
 
   const int q = blockIdx.x / a.k, rank = blockIdx.x - q * a.k;
