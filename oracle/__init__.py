@@ -10,6 +10,8 @@ builds it with gcc and exposes numpy-friendly wrappers:
 * ``sse`` / ``sse_many``  -- chi-square objective, Sec. 2.2 Eq. 2-2-4 with the
   model of Eq. 2-2-2 (c5 = 0) written in cycles.
 * ``de_solve``            -- DE/rand/1/bin with the Table 3-1-1 controls.
+* ``sse_full``, ``de_solve_full`` -- the full model of Eq. 2-2-2 (amplitude
+  slope c5) with the phase to order n = 4 (Sec. 3.2), 7 parameters.
 * ``de_textbook``         -- the same DE on sphere / Rosenbrock (self-check).
 * ``philox4x32_10``       -- Salmon et al. SC'11 counter-based generator.
 * ``theta_to_c``, ``c_phase``, ``c_freq``, ``c_total_phase`` -- Eq. 3-1-1 and
@@ -37,6 +39,9 @@ _lock = threading.Lock()
 _lib = None
 
 D = 5
+# the full model of Sec. 2.2: (A, phi0, f0, f1, f2, A1, f3), amplitude slope
+# c5 = A1 and the order-4 phase term f3 (cycles/s^4)
+DF = 7
 
 
 def build(force: bool = False) -> str:
@@ -96,6 +101,22 @@ def _load():
             fn.restype = ctypes.c_double
         lib.oc_theta_to_c.argtypes = [dp, dp]
         lib.oc_theta_to_c.restype = None
+        lib.oc_phase_cycles_full.argtypes = [dp, ctypes.c_double]
+        lib.oc_phase_cycles_full.restype = ctypes.c_double
+        lib.oc_model_full.argtypes = [dp, ctypes.c_double]
+        lib.oc_model_full.restype = ctypes.c_double
+        lib.oc_sse_full.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp]
+        lib.oc_sse_full.restype = ctypes.c_double
+        lib.oc_sse_full_many.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int64,
+                                         dp, ctypes.c_int]
+        lib.oc_sse_full_many.restype = None
+        lib.oc_de_solve_block_full.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_uint64, ctypes.c_uint32, dp, dp, dp, ctypes.c_int]
+        lib.oc_de_solve_block_full.restype = ctypes.c_int
+        lib.oc_de_textbook_dim.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_uint64, dp]
+        lib.oc_de_textbook_dim.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -209,6 +230,67 @@ def de_textbook(which: str, bounds, pop: int, gens: int, F: float, CR: float, se
     if rc != 0:
         raise ValueError("oracle de_textbook: invalid arguments")
     return out[:D].copy(), float(out[D])
+
+
+def phase_cycles_full(theta, t: float) -> float:
+    """p(t) = phi0/(2 pi) + f0 t + f1 t^2/2 + f2 t^3/6 + f3 t^4/24 (cycles)."""
+    th = _f64(theta)
+    return _load().oc_phase_cycles_full(_dptr(th), float(t))
+
+
+def model_full(theta, t: float) -> float:
+    """(A + A1 t) cos(2 pi p(t)): Eq. 2-2-2 with c5 = A1, phase to order 4."""
+    th = _f64(theta)
+    return _load().oc_model_full(_dptr(th), float(t))
+
+
+def sse_full(samples, fs: float, t0: float, theta) -> float:
+    """Eq. 2-2-4 objective of one full-model candidate (7 parameters)."""
+    s = _f64(samples)
+    th = _f64(theta)
+    return _load().oc_sse_full(_dptr(s), s.size, float(fs), float(t0), _dptr(th))
+
+
+def sse_full_many(samples, fs: float, t0: float, cands, nthreads: int = 0) -> np.ndarray:
+    s = _f64(samples)
+    c = _f64(cands).reshape(-1, DF)
+    out = np.zeros(c.shape[0], dtype=np.float64)
+    _load().oc_sse_full_many(_dptr(s), s.size, float(fs), float(t0), _dptr(c), c.shape[0], _dptr(out),
+                             int(nthreads))
+    return out
+
+
+def de_solve_full(samples, fs: float, t0: float, bounds, pop: int, gens: int, F: float, CR: float, seed: int,
+                  block_id: int = 0, nthreads: int = 0, return_population: bool = False):
+    """DE/rand/1/bin fit of the full model (7 parameters) on the chi-square.
+    A parameter whose bounds are equal is held there (A1 = 0 or f3 = 0 gives
+    the 6-parameter forms)."""
+    s = _f64(samples)
+    b = _f64(bounds).reshape(DF, 2)
+    out = np.zeros(DF + 1, dtype=np.float64)
+    popv = np.zeros((pop, DF), dtype=np.float64)
+    fit = np.zeros(pop, dtype=np.float64)
+    rc = _load().oc_de_solve_block_full(_dptr(s), s.size, float(fs), float(t0), _dptr(b), int(pop), int(gens),
+                                        float(F), float(CR), ctypes.c_uint64(int(seed)),
+                                        ctypes.c_uint32(int(block_id)), _dptr(out), _dptr(popv), _dptr(fit),
+                                        int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle de_solve_full: invalid arguments")
+    if return_population:
+        return out[:DF].copy(), float(out[DF]), popv, fit
+    return out[:DF].copy(), float(out[DF])
+
+
+def de_textbook_dim(which: str, bounds, pop: int, gens: int, F: float, CR: float, seed: int):
+    """The oracle's DE (rand/1/bin) on a textbook function of len(bounds) parameters (5 or 7)."""
+    b = _f64(bounds).reshape(-1, 2)
+    dim = b.shape[0]
+    out = np.zeros(dim + 1, dtype=np.float64)
+    rc = _load().oc_de_textbook_dim(0 if which == "sphere" else 1, dim, _dptr(b), int(pop), int(gens), float(F),
+                                    float(CR), ctypes.c_uint64(int(seed)), _dptr(out))
+    if rc != 0:
+        raise ValueError("oracle de_textbook_dim: invalid arguments")
+    return out[:dim].copy(), float(out[dim])
 
 
 def theta_to_c(theta) -> np.ndarray:

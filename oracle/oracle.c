@@ -11,6 +11,11 @@
  *     the Taylor phase of Eq. 2-2-1 / Eq. 2-2-3, re-parameterised in cycles:
  *       m(t) = A cos(2 pi p(t)),  p(t) = phi0/(2 pi) + f0 t + f1 t^2/2 + f2 t^3/6
  *     i.e. c0 = phi0, c1 = 2 pi f0, c2 = pi f1, c3 = pi f2 / 3, c4 = A.
+ *   - The full model: Eq. 2-2-2 with the amplitude slope c5 = A1 and the
+ *     phase of Eq. 2-2-1 taken to order n = 4 (Sec. 3.2, for arcs near
+ *     perigee), theta = (A, phi0, f0, f1, f2, A1, f3):
+ *       m(t) = (A + A1 t) cos(2 pi p(t)),  p(t) = ... + f3 t^4 / 24,
+ *     fitted on the chi-square by the same DE over 7 parameters.
  *   - Chi-square objective with unit weights, Sec. 2.2 Eq. 2-2-4:
  *       F(theta) = sum_i (s_i - m(t_i))^2.
  *   - Correlation objective, Sec. 2.2 Eq. 2-2-5 with the constant-amplitude
@@ -45,7 +50,9 @@
  *
  * Parity pins live in the test suite (closed-form tone sums, noise-energy
  * identities, brute-force grids, cuRAND/Random123 known answers, textbook
- * DE test functions, the paper's Appendix 1 worked example).
+ * DE test functions, the paper's Appendix 1 worked example; for the full
+ * model, finite differences of the quartic phase and closed-form sums at
+ * sixteenth-cycle sample phases).
  */
 #include <math.h>
 #include <stdint.h>
@@ -122,6 +129,44 @@ double oc_sse(const double* s, int64_t n, double fs, double t0, const double th[
     acc += (long double)res * (long double)res;
   }
   return (double)acc;
+}
+
+/* The full model of Sec. 2.2: Eq. 2-2-2 with the amplitude slope (c5) and the
+ * Taylor phase of Eq. 2-2-1 at order n = 4 (the paper's order for
+ * high-dynamics arcs near perigee, Sec. 3.2), theta = (A, phi0, f0, f1, f2,
+ * A1, f3):
+ *   m(t) = (A + A1 t) cos(2 pi p(t)),
+ *   p(t) = phi0/(2 pi) + f0 t + f1 t^2/2 + f2 t^3/6 + f3 t^4/24. */
+#define OC_DF 7
+
+double oc_phase_cycles_full(const double th[OC_DF], double t) {
+  return th[1] / (2.0 * OC_PI) + th[2] * t + th[3] * t * t / 2.0 + th[4] * t * t * t / 6.0 +
+         th[6] * t * t * t * t / 24.0;
+}
+
+double oc_model_full(const double th[OC_DF], double t) {
+  double p = oc_phase_cycles_full(th, t);
+  double r = p - nearbyint(p);
+  return (th[0] + th[5] * t) * cos(2.0 * OC_PI * r);
+}
+
+double oc_sse_full(const double* s, int64_t n, double fs, double t0, const double th[OC_DF]) {
+  long double acc = 0.0L;
+  for (int64_t i = 0; i < n; ++i) {
+    double t = t0 + (double)i / fs;
+    double res = s[i] - oc_model_full(th, t);
+    acc += (long double)res * (long double)res;
+  }
+  return (double)acc;
+}
+
+void oc_sse_full_many(const double* s, int64_t n, double fs, double t0, const double* cands, int64_t ncand,
+                      double* out, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int64_t c = 0; c < ncand; ++c) out[c] = oc_sse_full(s, n, fs, t0, cands + OC_DF * c);
 }
 
 /* Eq. 2-2-5 / 2-2-6: the unnormalised cross-correlation of the samples with
@@ -223,6 +268,16 @@ static void oc_pick3(uint32_t i, uint32_t np, const uint32_t w[3], uint32_t r[3]
 #define OC_DE_BEST1_JITTER 3
 #define OC_DE_EITHER_OR 6
 
+/* Sixteen words (counter groups 0..3) for individual ind at generation gen;
+ * the first twelve are oc_draw12's. */
+static void oc_draw16(uint64_t seed, uint32_t block_id, uint32_t gen, uint32_t ind, uint32_t w[16]) {
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  for (uint32_t g = 0; g < 4; ++g) {
+    uint32_t ctr[4] = {g, ind, gen, block_id};
+    oc_philox4x32_10(ctr, key, w + 4 * g);
+  }
+}
+
 /* The jitter and either-or words of individual ind at generation gen: words
  * 9..11 of the three-group draw, then a fourth counter group (word group 3). */
 static void oc_draw_extra(uint64_t seed, uint32_t block_id, uint32_t gen, uint32_t ind, uint32_t w4[4]) {
@@ -231,9 +286,16 @@ static void oc_draw_extra(uint64_t seed, uint32_t block_id, uint32_t gen, uint32
   oc_philox4x32_10(ctr, key, w4);
 }
 
+int oc_de_run_dim(oc_objective_fn obj, void* user, int dim, const double* bounds, int np, int gens, double F,
+                  double CR, uint64_t seed, uint32_t block_id, int strategy, double* out, double* final_pop,
+                  double* final_fit, int nthreads);
+
 int oc_de_run_strategy(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], int np, int gens, double F,
                        double CR, uint64_t seed, uint32_t block_id, int strategy, double out[OC_D + 1],
-                       double* final_pop, double* final_fit, int nthreads);
+                       double* final_pop, double* final_fit, int nthreads) {
+  return oc_de_run_dim(obj, user, OC_D, bounds, np, gens, F, CR, seed, block_id, strategy, out, final_pop, final_fit,
+                       nthreads);
+}
 
 /* Runs DE/rand/1/bin; returns 0 on success, -1 on invalid arguments.
  * out[0..4] = best vector, out[5] = its objective value.
@@ -245,13 +307,19 @@ int oc_de_run(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], in
                             final_fit, nthreads);
 }
 
-int oc_de_run_strategy(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], int np, int gens, double F,
-                       double CR, uint64_t seed, uint32_t block_id, int strategy, double out[OC_D + 1],
-                       double* final_pop, double* final_fit, int nthreads) {
-  if (np < 4 || gens < 0) return -1;
+/* DE over `dim` parameters: 5 for the cubic model, 7 for the full model (the
+ * strategies other than rand/1/bin are defined for 5). Generation 0 draws
+ * component j from words 2j and 2j+1 of oc_draw16 (the same words as
+ * oc_draw12's for dim 5); later generations draw as for dim 5, with the
+ * crossover word of component j at word 4 + j. */
+int oc_de_run_dim(oc_objective_fn obj, void* user, int dim, const double* bounds, int np, int gens, double F,
+                  double CR, uint64_t seed, uint32_t block_id, int strategy, double* out, double* final_pop,
+                  double* final_fit, int nthreads) {
+  if (np < 4 || gens < 0 || (dim != OC_D && dim != OC_DF)) return -1;
   if (strategy != OC_DE_RAND1_BIN && strategy != OC_DE_BEST1_JITTER && strategy != OC_DE_EITHER_OR) return -1;
-  double lo[OC_D], hi[OC_D];
-  for (int j = 0; j < OC_D; ++j) {
+  if (dim != OC_D && strategy != OC_DE_RAND1_BIN) return -1;
+  double lo[OC_DF], hi[OC_DF];
+  for (int j = 0; j < dim; ++j) {
     lo[j] = bounds[2 * j];
     hi[j] = bounds[2 * j + 1];
     if (!(lo[j] <= hi[j])) return -1;
@@ -261,22 +329,22 @@ int oc_de_run_strategy(oc_objective_fn obj, void* user, const double bounds[2 * 
 #else
   (void)nthreads;
 #endif
-  double* x = (double*)malloc(sizeof(double) * np * OC_D);
+  double* x = (double*)malloc(sizeof(double) * np * dim);
   double* fx = (double*)malloc(sizeof(double) * np);
-  double* u = (double*)malloc(sizeof(double) * np * OC_D);
+  double* u = (double*)malloc(sizeof(double) * np * dim);
   double* fu = (double*)malloc(sizeof(double) * np);
   if (!x || !fx || !u || !fu) { free(x); free(fx); free(u); free(fu); return -1; }
 
   /* Initial population: uniform inside the bounds (generation index 0). */
   for (int i = 0; i < np; ++i) {
-    uint32_t w[12];
-    oc_draw12(seed, block_id, 0u, (uint32_t)i, w);
-    for (int j = 0; j < OC_D; ++j) x[i * OC_D + j] = lo[j] + oc_u53(w[2 * j], w[2 * j + 1]) * (hi[j] - lo[j]);
+    uint32_t w[16];
+    oc_draw16(seed, block_id, 0u, (uint32_t)i, w);
+    for (int j = 0; j < dim; ++j) x[i * dim + j] = lo[j] + oc_u53(w[2 * j], w[2 * j + 1]) * (hi[j] - lo[j]);
   }
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
 #endif
-  for (int i = 0; i < np; ++i) fx[i] = obj(x + i * OC_D, user);
+  for (int i = 0; i < np; ++i) fx[i] = obj(x + i * dim, user);
 
   uint32_t cr_thr = CR >= 1.0 ? 0xffffffffu : (uint32_t)(CR * 4294967296.0);
   int cr_all = CR >= 1.0;
@@ -291,18 +359,18 @@ int oc_de_run_strategy(oc_objective_fn obj, void* user, const double bounds[2 * 
       uint32_t w[12], r[3], w4[4];
       oc_draw12(seed, block_id, (uint32_t)g, (uint32_t)i, w);
       oc_pick3((uint32_t)i, (uint32_t)np, w, r);
-      uint32_t jrand = oc_lemire(w[3], OC_D);
+      uint32_t jrand = oc_lemire(w[3], (uint32_t)dim);
       if (strategy == OC_DE_BEST1_JITTER) oc_draw_extra(seed, block_id, (uint32_t)g, (uint32_t)i, w4);
       const int three_point = strategy == OC_DE_EITHER_OR && w[9] >= 0x80000000u;
-      for (int j = 0; j < OC_D; ++j) {
-        double parent = x[i * OC_D + j];
-        const double a = x[r[0] * OC_D + j], b = x[r[1] * OC_D + j], c = x[r[2] * OC_D + j];
+      for (int j = 0; j < dim; ++j) {
+        double parent = x[i * dim + j];
+        const double a = x[r[0] * dim + j], b = x[r[1] * dim + j], c = x[r[2] * dim + j];
         double v;
         int take;
         if (strategy == OC_DE_BEST1_JITTER) {
           const uint32_t jw = j < 3 ? w[9 + j] : w4[j - 3];
           const double Fj = F + 1e-4 * ((double)jw * (1.0 / 4294967296.0));
-          v = x[best * OC_D + j] + Fj * (b - c);
+          v = x[best * dim + j] + Fj * (b - c);
           take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
         } else if (strategy == OC_DE_EITHER_OR) {
           v = three_point ? a + K * ((b + c) - 2.0 * a) : a + F * (b - c);
@@ -311,17 +379,17 @@ int oc_de_run_strategy(oc_objective_fn obj, void* user, const double bounds[2 * 
           v = a + F * (b - c);
           take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
         }
-        u[i * OC_D + j] = take ? oc_repair(j, v, parent, lo, hi) : parent;
+        u[i * dim + j] = take ? oc_repair(j, v, parent, lo, hi) : parent;
       }
     }
     /* evaluate all trials, then select (trial wins ties) */
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
 #endif
-    for (int i = 0; i < np; ++i) fu[i] = obj(u + i * OC_D, user);
+    for (int i = 0; i < np; ++i) fu[i] = obj(u + i * dim, user);
     for (int i = 0; i < np; ++i) {
       if (fu[i] <= fx[i]) {
-        memcpy(x + i * OC_D, u + i * OC_D, sizeof(double) * OC_D);
+        memcpy(x + i * dim, u + i * dim, sizeof(double) * dim);
         fx[i] = fu[i];
       }
     }
@@ -329,9 +397,9 @@ int oc_de_run_strategy(oc_objective_fn obj, void* user, const double bounds[2 * 
   int best = 0;
   for (int i = 1; i < np; ++i)
     if (fx[i] < fx[best]) best = i;
-  for (int j = 0; j < OC_D; ++j) out[j] = x[best * OC_D + j];
-  out[OC_D] = fx[best];
-  if (final_pop) memcpy(final_pop, x, sizeof(double) * np * OC_D);
+  for (int j = 0; j < dim; ++j) out[j] = x[best * dim + j];
+  out[dim] = fx[best];
+  if (final_pop) memcpy(final_pop, x, sizeof(double) * np * dim);
   if (final_fit) memcpy(final_fit, fx, sizeof(double) * np);
   free(x); free(fx); free(u); free(fu);
   return 0;
@@ -358,6 +426,21 @@ int oc_de_solve_block_obj(const double* s, int64_t n, double fs, double t0, cons
   oc_block b = {s, n, fs, t0};
   return oc_de_run_strategy(objective ? oc_block_cor_objective : oc_block_objective, &b, bounds, np, gens, F, CR,
                             seed, block_id, strategy, out, final_pop, final_fit, nthreads);
+}
+
+static double oc_block_full_objective(const double* th, void* user) {
+  const oc_block* b = (const oc_block*)user;
+  return oc_sse_full(b->s, b->n, b->fs, b->t0, th);
+}
+
+/* DE/rand/1/bin fit of the full model (7 parameters) on the chi-square. */
+int oc_de_solve_block_full(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_DF], int np,
+                           int gens, double F, double CR, uint64_t seed, uint32_t block_id, double out[OC_DF + 1],
+                           double* final_pop, double* final_fit, int nthreads) {
+  if (n < 1 || !(fs > 0.0)) return -1;
+  oc_block b = {s, n, fs, t0};
+  return oc_de_run_dim(oc_block_full_objective, &b, OC_DF, bounds, np, gens, F, CR, seed, block_id, OC_DE_RAND1_BIN,
+                       out, final_pop, final_fit, nthreads);
 }
 
 int oc_de_solve_block(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_D], int np,
@@ -394,6 +477,30 @@ int oc_de_textbook_strategy(int which, const double bounds[2 * OC_D], int np, in
                             uint64_t seed, int strategy, double out[OC_D + 1]) {
   oc_objective_fn f = which == 0 ? oc_sphere : oc_rosenbrock;
   return oc_de_run_strategy(f, NULL, bounds, np, gens, F, CR, seed, 0u, strategy, out, NULL, NULL, 1);
+}
+
+/* The same textbook functions over `dim` parameters (the dimension rides in
+ * `user`), for the DE over the full model's 7 parameters. */
+static double oc_sphere_n(const double* x, void* user) {
+  const int dim = *(const int*)user;
+  double s = 0.0;
+  for (int j = 0; j < dim; ++j) s += x[j] * x[j];
+  return s;
+}
+static double oc_rosenbrock_n(const double* x, void* user) {
+  const int dim = *(const int*)user;
+  double s = 0.0;
+  for (int j = 0; j + 1 < dim; ++j) {
+    double a = x[j + 1] - x[j] * x[j], b = 1.0 - x[j];
+    s += 100.0 * a * a + b * b;
+  }
+  return s;
+}
+
+int oc_de_textbook_dim(int which, int dim, const double* bounds, int np, int gens, double F, double CR,
+                       uint64_t seed, double* out) {
+  oc_objective_fn f = which == 0 ? oc_sphere_n : oc_rosenbrock_n;
+  return oc_de_run_dim(f, &dim, dim, bounds, np, gens, F, CR, seed, 0u, OC_DE_RAND1_BIN, out, NULL, NULL, 1);
 }
 
 /* ------------------------------------------------------------------------ */

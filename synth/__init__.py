@@ -21,6 +21,8 @@ Workloads:
 * ``batch``        256 blocks, N log-uniform in [5e4, 1e6], fs log-uniform in
                    [1, 50] kHz, pop uniform in 32..128, G = ceil(80000/pop).
 * ``stream``       continuous-phase station streams for the serving loop.
+* ``perigee400k``  the paper400k shape for the full model (amplitude slope
+                   and quartic phase term, 7 parameters).
 """
 from __future__ import annotations
 
@@ -42,10 +44,10 @@ class Block:
     scale: float                 # physical value = scale * stored value
     fs: float                    # sampling rate, Hz
     t0: float                    # time of sample 0 (s); centred blocks use -(N-1)/(2 fs)
-    truth: np.ndarray            # (A, phi0, f0, f1, f2)
+    truth: np.ndarray            # (A, phi0, f0, f1, f2) [+ (A1, f3) for the full model]
     sigma: float                 # noise standard deviation
     snr_db: float
-    bounds: np.ndarray           # (5, 2) lo, hi
+    bounds: np.ndarray           # (5, 2) lo, hi  [(7, 2) for the full model]
     pop: int = 64
     gens: int = 1250
     F: float = 0.7
@@ -177,6 +179,47 @@ def paper400k(seed: int = 0, n: int = 400_000, fs: float = 10_000.0, storage: in
 def precision(seed: int, storage: int, n: int = 400_000, fs: float = 10_000.0, gens: int = 1250) -> Block:
     """The paper400k analog signal of ``seed`` stored as ``storage`` (precision sweep)."""
     return paper400k(seed, n=n, fs=fs, storage=storage, gens=gens)
+
+
+def clean_tone_full(truth, n: int, fs: float, t0: float) -> np.ndarray:
+    """Noise-free (A + A1 t) cos(phi0 + 2 pi (f0 t + f1 t^2/2 + f2 t^3/6 + f3 t^4/24))
+    for truth = (A, phi0, f0, f1, f2, A1, f3)."""
+    A, phi0, f0, f1, f2, A1, f3 = [float(v) for v in truth]
+    t = t0 + np.arange(n, dtype=np.float64) / fs
+    return (A + A1 * t) * np.cos(phi0 + 2.0 * np.pi * (f0 * t + f1 * t * t / 2.0 + f2 * t ** 3 / 6.0
+                                                       + f3 * t ** 4 / 24.0))
+
+
+def perigee400k(seed: int = 0, n: int = 400_000, fs: float = 10_000.0, storage: int = I16, pop: int = 64,
+                gens: int = 1250, snr_range=(10.0, 30.0)) -> Block:
+    """Paper-size block of a high-dynamics arc (near perigee, where the paper
+    takes the phase to order n = 4): N = 400,000 samples at 10 kHz, int16;
+    the paper400k ranges for A, phi0, f0, f1, f2, plus an amplitude slope
+    A1 ~ U(-0.1, 0.1) A / T and a quartic term f3 ~ U(-5e-4, 5e-4) cycles/s^4
+    (a fourth phase derivative up to ~3e-3 rad/s^4, the order of the perigee
+    figure of Sec. 3.2). truth and bounds have 7 rows (A, phi0, f0, f1, f2, A1,
+    f3); A1's range is the paper's +-0.2 A / T, f3's window is +-192 / T^4
+    (about +-pi rad at the block edge) around the truth, offset like the
+    others."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7_000_003))
+    T = n / fs
+    A = rng.uniform(0.5, 2.0)
+    truth = np.array([A, rng.uniform(-math.pi, math.pi), rng.uniform(-2000.0, 2000.0), rng.uniform(-5.0, 5.0),
+                      rng.uniform(-0.05, 0.05), rng.uniform(-0.1, 0.1) * A / T, rng.uniform(-5e-4, 5e-4)])
+    snr_db = rng.uniform(*snr_range)
+    sigma = _sigma_for(A, snr_db)
+    t0 = centred_t0(n, fs)
+    noise = rng.normal(0.0, sigma, n)
+    x = clean_tone_full(truth, n, fs, t0) + noise
+    b5 = paper_bounds(rng, truth[:5], T)
+    bounds = np.zeros((7, 2))
+    bounds[:5] = b5
+    bounds[5] = (-0.2 * b5[0, 1] / T, 0.2 * b5[0, 1] / T)
+    bounds[6] = _window(rng, truth[6], 192.0 / T ** 4)
+    peak = truth[0] + abs(truth[5]) * T / 2
+    stored, scale = quantise(x, peak + 6.0 * sigma, storage)
+    return Block(stored, storage, scale, fs, t0, truth, sigma, snr_db, bounds, pop=pop, gens=gens, F=0.7, CR=0.9,
+                 de_seed=seed, block_id=0, noise=noise)
 
 
 def batch(seed: int = 0, nblocks: int = 256, n_lo: int = 50_000, n_hi: int = 1_000_000, fs_lo: float = 1_000.0,
