@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 WORKLOAD = "paper400k_int16_pop64_g1250"
+WORKLOAD_FULL = "perigee400k_int16_pop64_g1250_full_model"
 METRIC = "objective sample-evals/s"
 UNIT = "sample-evals/s"
 # paper: 400K-sample block, ~80,000 objective evaluations, 6.5 s on a GTX580 (Sec. 1.3)
@@ -138,21 +139,22 @@ class ClockSampler:
                 "samples": len(sm), "sm_mhz_min": float(min(sm))}
 
 
-def cpu_baseline(blk: synth.Block, gens: int = 240):
+def cpu_baseline(blk: synth.Block, gens: int = 240, full: bool = False):
     """The oracle (FP64, libm cos, OpenMP over candidates) timed on this host's
     cores on a bounded sample of the workload: the same block and population
-    for `gens` generations instead of 1250."""
+    for `gens` generations instead of 1250 (the full model's fit with full)."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
     s = blk.values()
     t = time.perf_counter()
-    oracle.de_solve(s, blk.fs, blk.t0, blk.bounds, blk.pop, gens, blk.F, blk.CR, blk.de_seed, nthreads=cores)
+    solve = oracle.de_solve_full if full else oracle.de_solve
+    solve(s, blk.fs, blk.t0, blk.bounds, blk.pop, gens, blk.F, blk.CR, blk.de_seed, nthreads=cores)
     dt = time.perf_counter() - t
     evals = blk.n * blk.pop * (gens + 1)
     return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"oracle DE on the 400K int16 block, pop {blk.pop}, {gens} generations "
-                      f"({evals:.3g} sample-evals, {dt:.1f} s)"}
+            "sample": f"oracle DE{' (full model)' if full else ''} on the 400K int16 block, pop {blk.pop}, "
+                      f"{gens} generations ({evals:.3g} sample-evals, {dt:.1f} s)"}
 
 
 def run_reference(args):
@@ -191,7 +193,8 @@ def run_gpu(args):
     build.build()
     # one paper-size block per rank (equal costs: the router gives rank r block r)
     (unit,) = replicas.my_units([1.0] * world, world, rank)
-    blk = synth.paper400k(unit, gens=args.gens)
+    full = args.model == "full"
+    blk = synth.perigee400k(unit, gens=args.gens) if full else synth.paper400k(unit, gens=args.gens)
     ctx = pt.Context(local)
     # a dedicated stream: the library launches on it and the CUDA events below
     # are recorded on it, so they bracket exactly the library's work
@@ -208,6 +211,8 @@ def run_gpu(args):
     evals = blk.sample_evals()
 
     def step():
+        if full:
+            return ctx.de_solve_full(bounds, blk.pop, blk.gens, blk.F, blk.CR, blk.de_seed)
         return ctx.de_solve(bounds, blk.pop, blk.gens, blk.F, blk.CR, blk.de_seed, pt.TIER_F64)
 
     for _ in range(args.warmup):
@@ -253,7 +258,9 @@ def run_gpu(args):
     peak = SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6
     traffic, traffic_note = profiled_traffic()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-            "traffic": traffic, "traffic_note": traffic_note, "kernel": "k_de<TIER_F64>",
+            "traffic": None if full else traffic,
+            "traffic_note": "no ncu capture of the full-model kernel" if full else traffic_note,
+            "kernel": "k_de<TIER_F64, OBJ_CHI2, MODEL_FULL>" if full else "k_de<TIER_F64>",
             "peak_basis": "148 SMs x 16 SFU cosines/clk x 2032 MHz (one cosine per sample-eval)"}
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (SMS * SFU_PER_CLK * clocks["sm_mhz"] * 1e6)
@@ -261,16 +268,18 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": value / world / PAPER_SAMPLE_EVALS_PER_S, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": blk.n, "fs": blk.fs, "storage": "int16", "pop": blk.pop,
-                       "gens": blk.gens, "tier": "f64-anchored phase, f32 cos", "l2": "flushed between steps",
+            "config": {"workload": WORKLOAD_FULL if full else WORKLOAD, "n": blk.n, "fs": blk.fs,
+                       "storage": "int16", "pop": blk.pop, "gens": blk.gens,
+                       "model": "full (A, phi0, f0, f1, f2, A1, f3)" if full else "cubic (A, phi0, f0, f1, f2)",
+                       "tier": "f64-anchored phase, f32 cos", "l2": "flushed between steps",
                        "objective": "chi-square (Eq. 2-2-4)" if args.objective == "chi2" else
                        "correlation (Eq. 2-2-5, constant A)",
                        "de_seconds": total_ms / args.steps * 1e-3, "wall_s": wall},
             "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(blk.samples.nbytes),
-                    "d2h_bytes_per_step": 6 * 8 + 8}}
+                    "d2h_bytes_per_step": (len(params) + 1) * 8 + 8}}
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(blk) if world == 1 else None
+        line["cpu_baseline"] = cpu_baseline(blk, full=full) if world == 1 else None
     if rank == 0:
         line["fit"] = {"params": [float(v) for v in params], "sse": float(sse), "truth": [float(v) for v in blk.truth]}
         print(json.dumps(line))
@@ -650,6 +659,9 @@ def main():
     ap.add_argument("--ncand", type=int, default=4096, help="objective: candidates per call")
     ap.add_argument("--objective", default="chi2", choices=["chi2", "cor"],
                     help="single: the objective minimised (cor: Eq. 2-2-5 with A held at the block's amplitude)")
+    ap.add_argument("--model", default="cubic", choices=["cubic", "full"],
+                    help="single: the cubic model (default) or the full model (amplitude slope, order-4 phase) "
+                         "on the perigee-shaped 400K block")
     ap.add_argument("--nblocks", type=int, default=256)
     ap.add_argument("--speedup", type=float, default=20.0, help="serve: real-time compression factor")
     ap.add_argument("--sim-seconds", type=float, default=120.0, help="serve: simulated stream duration")

@@ -186,6 +186,36 @@ PT_API int pt_de_solve(pt_ctx* ctx, const double* bounds, int pop, int gens, dou
 PT_API int pt_de_solve_ex(pt_ctx* ctx, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
                    uint32_t block_id, double* params_out, double* pop_out, double* fit_out, int tier);
 
+/* ---- The full model -------------------------------------------------------
+ * Eq. 2-2-2 with the amplitude slope c5 and the Taylor phase of Eq. 2-2-1 at
+ * order n = 4 (Sec. 3.2, for high-dynamics arcs near perigee), 7 parameters
+ * theta = (A, phi0, f0, f1, f2, A1, f3):
+ *   m(t) = (A + A1 t) cos(phi0 + 2 pi (f0 t + f1 t^2/2 + f2 t^3/6 + f3 t^4/24)),
+ * i.e. c4 = A, c5 = A1 and the order-4 phase coefficient f3 (cycles/s^4). The
+ * default tier (PT_TIER_F64 arithmetic) and the chi-square of Eq. 2-2-4 only:
+ * both calls fail with PT_EINVAL unless the context's objective is
+ * PT_OBJ_CHI2 and its strategy PT_DE_RAND1_BIN. A parameter held at lo = hi
+ * stays there, so A1 = 0 or f3 = 0 gives the 6-parameter forms. */
+
+/* Evaluate Eq. 2-2-4 of the full model for n candidates on the loaded block.
+ *   cands    host or device pointer, n rows of 7 doubles, row-major.
+ *   sse_out  host or device pointer, n doubles.
+ * Deterministic (independent of the launch shape).
+ * Errors: PT_EINVAL, PT_ENOBLOCK, PT_ENOMEM, PT_ECUDA, PT_ETIMEOUT. */
+PT_API int pt_objective_full(pt_ctx* ctx, const double* cands, int64_t n, double* sse_out);
+
+/* Fit the loaded block with the full model by DE/rand/1/bin, as
+ * pt_de_solve_ex over 7 parameters. The draws are pt_de_solve_ex's, with the
+ * generation-0 words 12 and 13 of component 6 from counter (3, i, 0, block_id)
+ * and the crossover words of components 5, 6 at words 9, 10.
+ *   bounds      host pointer, 7 x 2 doubles.
+ *   params_out  host or device pointer, 8 doubles: the best theta and its SSE.
+ *   pop_out     optional host or device pointer, pop x 7 doubles.
+ *   fit_out     optional host or device pointer, pop doubles.
+ * Errors: PT_EINVAL, PT_ENOBLOCK, PT_ENOMEM, PT_ECUDA, PT_ETIMEOUT. */
+PT_API int pt_de_solve_full(pt_ctx* ctx, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
+                            uint32_t block_id, double* params_out, double* pop_out, double* fit_out);
+
 /* ---- Batched fits ---------------------------------------------------------
  * Many independent blocks of uneven length, each with its own DE controls and
  * population, solved in one persistent cooperative launch (replayed from a

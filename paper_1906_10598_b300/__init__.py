@@ -76,6 +76,11 @@ def load_library():
     lib.pt_de_solve_ex.argtypes = [vp, dp, c_int, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                    ctypes.c_uint32, vp, vp, vp, c_int]
     lib.pt_de_solve_ex.restype = c_int
+    lib.pt_objective_full.argtypes = [vp, vp, i64, vp]
+    lib.pt_objective_full.restype = c_int
+    lib.pt_de_solve_full.argtypes = [vp, dp, c_int, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                     ctypes.c_uint32, vp, vp, vp]
+    lib.pt_de_solve_full.restype = c_int
     lib.pt_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.pt_last_kernel_ms.restype = c_int
     _lib = lib
@@ -164,22 +169,31 @@ class Context:
                                             float(fs), float(t0)))
         self.n = n
 
+    @staticmethod
+    def _cands_out(cands, dim: int, out):
+        if isinstance(cands, np.ndarray):
+            c = np.ascontiguousarray(cands, dtype=np.float64).reshape(-1, dim)
+            if out is None:
+                out = np.zeros(c.shape[0], dtype=np.float64)
+        else:
+            c = cands.contiguous().reshape(-1, dim)
+            if out is None:
+                import torch
+                out = torch.empty(c.shape[0], dtype=torch.float64, device=c.device)
+        return c, c.shape[0], out
+
     def objective(self, cands, tier: int = TIER_F64, out=None):
         """pt_objective: SSE of each row of ``cands`` (n x 5). Returns ``out``
         (numpy float64 if cands is numpy, else a torch tensor on the same device)."""
-        if isinstance(cands, np.ndarray):
-            c = np.ascontiguousarray(cands, dtype=np.float64).reshape(-1, 5)
-            n = c.shape[0]
-            if out is None:
-                out = np.zeros(n, dtype=np.float64)
-        else:
-            c = cands.contiguous().reshape(-1, 5)
-            n = c.shape[0]
-            if out is None:
-                import torch
-                out = torch.empty(n, dtype=torch.float64, device=c.device)
+        c, n, out = self._cands_out(cands, 5, out)
         self._check(self._lib.pt_objective(self._h, ctypes.c_void_p(_ptr(c)), n, ctypes.c_void_p(_ptr(out)),
                                            int(tier)))
+        return out
+
+    def objective_full(self, cands, out=None):
+        """pt_objective_full: SSE of each full-model row (A, phi0, f0, f1, f2, A1, f3)."""
+        c, n, out = self._cands_out(cands, 7, out)
+        self._check(self._lib.pt_objective_full(self._h, ctypes.c_void_p(_ptr(c)), n, ctypes.c_void_p(_ptr(out))))
         return out
 
     def de_solve(self, bounds, pop: int, gens: int, F: float, CR: float, seed: int, tier: int = TIER_F64,
@@ -197,6 +211,23 @@ class Context:
         if return_population:
             return out[:5].copy(), float(out[5]), popv, fit
         return out[:5].copy(), float(out[5])
+
+    def de_solve_full(self, bounds, pop: int, gens: int, F: float, CR: float, seed: int, block_id: int = 0,
+                      return_population: bool = False):
+        """pt_de_solve_full: the full model's fit; returns (params[7], sse) or
+        (params, sse, population[pop, 7], fitness)."""
+        b = np.ascontiguousarray(np.asarray(bounds, dtype=np.float64).reshape(7, 2))
+        out = np.zeros(8, dtype=np.float64)
+        popv = np.zeros((pop, 7), dtype=np.float64) if return_population else None
+        fit = np.zeros(pop, dtype=np.float64) if return_population else None
+        self._check(self._lib.pt_de_solve_full(
+            self._h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(pop), int(gens), float(F), float(CR),
+            ctypes.c_uint64(int(seed)), ctypes.c_uint32(int(block_id)), ctypes.c_void_p(out.ctypes.data),
+            ctypes.c_void_p(popv.ctypes.data if popv is not None else 0),
+            ctypes.c_void_p(fit.ctypes.data if fit is not None else 0)))
+        if return_population:
+            return out[:7].copy(), float(out[7]), popv, fit
+        return out[:7].copy(), float(out[7])
 
     def last_kernel_ms(self) -> float:
         v = ctypes.c_float()

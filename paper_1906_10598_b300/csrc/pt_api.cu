@@ -15,7 +15,9 @@
 #include "pt_internal.h"
 #include "pt_kernels.cuh"
 
-static_assert(pt::HOST_NP_MAX == pt::NP_MAX && pt::HOST_RING_STRIDE == pt::RING_STRIDE && pt::HOST_L == pt::L,
+static_assert(pt::HOST_NP_MAX == pt::NP_MAX && pt::HOST_RING_STRIDE == pt::RING_STRIDE && pt::HOST_L == pt::L &&
+                  pt::HOST_D == pt::D && pt::HOST_DMAX == pt::DF && pt::HOST_MODEL_CUBIC == pt::MODEL_CUBIC &&
+                  pt::HOST_MODEL_FULL == pt::MODEL_FULL,
               "host mirrors of the device constants");
 
 namespace pt {
@@ -77,12 +79,14 @@ BlockArgs to_block_args(const HostBlock& h) {
   b.t0cu_6 = h.t0 * h.t0 * h.t0 / 6.0;
   b.h2_2 = b.h * b.h / 2.0;
   b.h3_6 = b.h * b.h * b.h / 6.0;
+  b.t0qu_24 = h.t0 * h.t0 * h.t0 * h.t0 / 24.0;
+  b.h4_24 = b.h * b.h * b.h * b.h / 24.0;
   return b;
 }
 
 // ---- objective -------------------------------------------------------------
 
-template <int TIER, int CGV, int OBJ = OBJ_CHI2>
+template <int TIER, int CGV, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
   ObjArgs a{};
   a.b = to_block_args(c->blk);
@@ -99,17 +103,23 @@ int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
   a.acc = c->d_acc;
   a.err = c->d_err;
   a.timeout_ns = c->timeout_ns;
-  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, a.b.esize, 0, NT);
+  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, a.b.esize, 0, NT, MODEL);
   if (S.total > c->smem_optin) return fail(c, PT_EINVAL, "objective launch needs too much shared memory");
-  PT_CUDA(c, cudaFuncSetAttribute(k_objective<TIER, CGV, OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PT_CUDA(c, cudaFuncSetAttribute(k_objective<TIER, CGV, OBJ, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)S.total));
   dim3 grid(nx, ny);
-  k_objective<TIER, CGV, OBJ><<<grid, NT, S.total, c->stream>>>(a);
+  k_objective<TIER, CGV, OBJ, MODEL><<<grid, NT, S.total, c->stream>>>(a);
   PT_CUDA(c, cudaGetLastError());
   return PT_OK;
 }
 
-int launch_objective_any(pt_ctx* c, int tier, const double* d_cands, int ncand) {
+int launch_objective_any(pt_ctx* c, int tier, const double* d_cands, int ncand, int model) {
+  if (model == MODEL_FULL) {
+    const int cg = pick_cg(PT_TIER_F64, std::min(ncand, NP_MAX));
+    if (cg == 16) return launch_objective<TIER_F64, 16, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+    if (cg == 8) return launch_objective<TIER_F64, 8, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+    return launch_objective<TIER_F64, 4, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+  }
   if (c->objective == PT_OBJ_COR) {
     if (tier != PT_TIER_F64) return fail(c, PT_EINVAL, "the correlation objective runs in the default tier only");
     const int cg = pick_cg(tier, std::min(ncand, NP_MAX));
@@ -132,23 +142,23 @@ int launch_objective_any(pt_ctx* c, int tier, const double* d_cands, int ncand) 
 
 // ---- grouped DE --------------------------------------------------------------
 
-size_t smem_de(int tier, int sc_tiles, int esize_max) {
-  return smem_layout(tier, NP_MAX, sc_tiles, 16, esize_max, NP_MAX, NT).total;
+size_t smem_de(int tier, int sc_tiles, int esize_max, int model) {
+  return smem_layout(tier, NP_MAX, sc_tiles, 16, esize_max, NP_MAX, NT, model).total;
 }
 
-template <int TIER, int OBJ = OBJ_CHI2>
+template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 int launch_de_t(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
-  const size_t smem = smem_de(TIER, a.sc_tiles, a.esize_max);
+  const size_t smem = smem_de(TIER, a.sc_tiles, a.esize_max, MODEL);
   cudaFuncAttributes fa{};
-  PT_CUDA(c, cudaFuncGetAttributes(&fa, k_de<TIER, OBJ>));
+  PT_CUDA(c, cudaFuncGetAttributes(&fa, k_de<TIER, OBJ, MODEL>));
   if (smem + fa.sharedSizeBytes > c->smem_optin) return fail(c, PT_EINVAL, "DE launch needs too much shared memory");
-  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, OBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, OBJ, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, OBJ>, NT, smem));
+  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, OBJ, MODEL>, NT, smem));
   const int grid = a.ngroups * a.k;
   if (occ < 1 || grid > occ * c->sms) return fail(c, PT_EINVAL, "DE grid cannot be co-resident");
   void* args[] = {&a};
-  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, OBJ>, dim3(grid), dim3(NT), args, smem, s));
+  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, OBJ, MODEL>, dim3(grid), dim3(NT), args, smem, s));
   return PT_OK;
 }
 
@@ -164,9 +174,9 @@ size_t de_desc_bytes(int nblocks, int ngroups) { return o_off(nblocks) + (size_t
 // under 1 KB) comes out of the same per-block opt-in budget as the dynamic part.
 constexpr size_t DE_STATIC_SMEM_RESERVE = 2048;
 
-int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want) {
+int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want, int model) {
   int sc = (int)std::max<int64_t>(1, std::min<int64_t>(want, 96));
-  while (sc > 1 && smem_de(tier, sc, esize_max) + DE_STATIC_SMEM_RESERVE > c->smem_optin) sc--;
+  while (sc > 1 && smem_de(tier, sc, esize_max, model) + DE_STATIC_SMEM_RESERVE > c->smem_optin) sc--;
   return sc;
 }
 
@@ -211,12 +221,12 @@ int load_samples(pt_ctx* c, cudaStream_t s, const void* samples, int64_t n, int 
   return PT_OK;
 }
 
-int check_de_args(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, int tier) {
+int check_de_args(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, int tier, int dim) {
   if (!bounds || pop < 4 || pop > PT_POP_MAX || gens < 0 || !valid_tier(tier) || !std::isfinite(F) ||
       !std::isfinite(CR) || CR < 0.0)
     return fail(c, PT_EINVAL, "DE: invalid argument");
   if (is_device_ptr(bounds)) return fail(c, PT_EINVAL, "DE: bounds must be a host pointer");
-  for (int j = 0; j < D; ++j) {
+  for (int j = 0; j < dim; ++j) {
     const double lo = bounds[2 * j], hi = bounds[2 * j + 1];
     if (!std::isfinite(lo) || !std::isfinite(hi) || lo > hi)
       return fail(c, PT_EINVAL, "DE: bounds must be finite with lo <= hi");
@@ -230,7 +240,7 @@ namespace pt {
 
 int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blocks, int nblocks, const int* sched,
                      const int* off, int ngroups, int k, void* d_desc_buf, unsigned long long* ring, int* d_err,
-                     int mode) {
+                     int mode, int model) {
   std::vector<DeBlockDesc> desc(nblocks);
   int esize_max = 1;
   int64_t want = 1;
@@ -238,9 +248,9 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
     const HostDeBlock& h = blocks[i];
     DeBlockDesc& d = desc[i];
     d.b = to_block_args(h.blk);
-    for (int j = 0; j < D; ++j) {
-      d.dc.lo[j] = h.lo[j];
-      d.dc.hi[j] = h.hi[j];
+    for (int j = 0; j < DF; ++j) {
+      d.dc.lo[j] = j < model_dim(model) ? h.lo[j] : 0.0;
+      d.dc.hi[j] = j < model_dim(model) ? h.hi[j] : 0.0;
     }
     d.dc.F = h.F;
     d.dc.K = (h.F + 1.0) * 0.5;
@@ -273,7 +283,7 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   a.sched_off = (const int*)(base + o_off(nblocks));
   a.ngroups = ngroups;
   a.k = k;
-  a.sc_tiles = pick_sc_tiles(c, tier, esize_max, want);
+  a.sc_tiles = pick_sc_tiles(c, tier, esize_max, want, model);
   a.esize_max = esize_max;
   a.ring = ring;
   a.err = d_err;
@@ -281,6 +291,11 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   if (!(mode & DE_LAUNCH)) return PT_OK;
   PT_CUDA(c, cudaMemsetAsync(ring, 0, (size_t)ngroups * RING_GROUP_WORDS * sizeof(unsigned long long), s));
   PT_CUDA(c, cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  if (model == MODEL_FULL) {
+    // the full model: default tier, chi-square, DE/rand/1/bin (checked by the entry point)
+    a.obj = OBJ_CHI2;
+    return launch_de_t<TIER_F64, OBJ_CHI2, MODEL_FULL>(c, s, a);
+  }
   a.obj = c->objective;
   if (a.obj == OBJ_COR) {
     if (tier != PT_TIER_F64) return fail(c, PT_EINVAL, "the correlation objective runs in the default tier only");
@@ -344,7 +359,7 @@ int pt_create(pt_ctx** out, int device) {
   if (bad(cudaMalloc(&c->d_ring, (size_t)c->sms * RING_GROUP_WORDS * sizeof(unsigned long long)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_err, sizeof(int)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_out, 8 * sizeof(double)))) return PT_ENOMEM;
-  if (bad(cudaMalloc(&c->d_pop, PT_POP_MAX * D * sizeof(double)))) return PT_ENOMEM;
+  if (bad(cudaMalloc(&c->d_pop, PT_POP_MAX * DF * sizeof(double)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_fit, PT_POP_MAX * sizeof(double)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_u64, sizeof(unsigned long long)))) return PT_ENOMEM;
   if (bad(cudaMalloc(&c->d_desc, de_desc_bytes(1, 1)))) return PT_ENOMEM;
@@ -413,8 +428,13 @@ int pt_load_block(pt_ctx* c, const void* samples, int64_t n, int dtype, double s
   return PT_OK;
 }
 
-int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int tier) {
-  if (!c) return PT_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// pt_objective / pt_objective_full: candidates of model_dim(model) parameters.
+int objective_impl(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int tier, int model) {
+  const int dim = model_dim(model);
   if (!cands || !sse_out || n < 1 || n > (1 << 24) || !valid_tier(tier))
     return fail(c, PT_EINVAL, "pt_objective: invalid argument");
   if (!c->has_block) return fail(c, PT_ENOBLOCK, "pt_objective: no block loaded");
@@ -424,8 +444,8 @@ int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int
   if ((rc = ensure(c, &c->d_sse, &c->sse_cap, (size_t)n)) != PT_OK) return rc;
   const double* d_c = cands;
   if (!is_device_ptr(cands)) {
-    if ((rc = ensure(c, &c->d_cands, &c->cands_cap, (size_t)n * D)) != PT_OK) return rc;
-    PT_CUDA(c, cudaMemcpyAsync(c->d_cands, cands, (size_t)n * D * sizeof(double), cudaMemcpyHostToDevice,
+    if ((rc = ensure(c, &c->d_cands, &c->cands_cap, (size_t)n * dim)) != PT_OK) return rc;
+    PT_CUDA(c, cudaMemcpyAsync(c->d_cands, cands, (size_t)n * dim * sizeof(double), cudaMemcpyHostToDevice,
                                c->stream));
     d_c = c->d_cands;
   }
@@ -434,10 +454,11 @@ int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int
   PT_CUDA(c, cudaMemsetAsync(c->d_acc, 0, (size_t)n * sizeof(unsigned long long), c->stream));
   PT_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   PT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-  rc = launch_objective_any(c, tier, d_c, (int)n);
+  rc = launch_objective_any(c, tier, d_c, (int)n, model);
   if (rc != PT_OK) return rc;
   k_finalize<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(d_c, (int)n, c->d_acc, c->blk.n, (float)c->blk.smax,
-                                                             d_out, c->objective);
+                                                             d_out, c->objective, model, c->blk.t0,
+                                                             1.0 / c->blk.fs);
   PT_CUDA(c, cudaGetLastError());
   PT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   if (!dev_out)
@@ -447,17 +468,19 @@ int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int
   return PT_OK;
 }
 
-int pt_de_solve_ex(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
-                   uint32_t block_id, double* params_out, double* pop_out, double* fit_out, int tier) {
-  if (!c) return PT_EINVAL;
-  int rc = check_de_args(c, bounds, pop, gens, F, CR, tier);
+// pt_de_solve_ex / pt_de_solve_full: bounds, params_out and pop_out of
+// model_dim(model) parameters.
+int de_solve_impl(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
+                  uint32_t block_id, double* params_out, double* pop_out, double* fit_out, int tier, int model) {
+  const int dim = model_dim(model);
+  int rc = check_de_args(c, bounds, pop, gens, F, CR, tier, dim);
   if (rc != PT_OK) return rc;
   if (!params_out) return fail(c, PT_EINVAL, "pt_de_solve: params_out is null");
   if (!c->has_block) return fail(c, PT_ENOBLOCK, "pt_de_solve: no block loaded");
   PT_CUDA(c, cudaSetDevice(c->device));
   HostDeBlock h;
   h.blk = c->blk;
-  for (int j = 0; j < D; ++j) {
+  for (int j = 0; j < dim; ++j) {
     h.lo[j] = bounds[2 * j];
     h.hi[j] = bounds[2 * j + 1];
   }
@@ -474,18 +497,57 @@ int pt_de_solve_ex(pt_ctx* c, const double* bounds, int pop, int gens, double F,
   const int k = (int)std::min<int64_t>(c->blk.ntiles, c->sms);
   PT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   rc = launch_de_groups(c, c->stream, tier, &h, 1, sched, off, 1, k, c->d_desc, c->d_ring, c->d_err,
-                        DE_UPLOAD | DE_LAUNCH);
+                        DE_UPLOAD | DE_LAUNCH, model);
   if (rc != PT_OK) return rc;
   PT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   if ((rc = kernel_status(c, c->stream, c->d_err)) != PT_OK) return rc;
   PT_CUDA(c, cudaEventElapsedTime(&c->last_ms, c->ev0, c->ev1));
-  PT_CUDA(c, cudaMemcpyAsync(params_out, c->d_out, (D + 1) * sizeof(double), cudaMemcpyDefault, c->stream));
+  PT_CUDA(c, cudaMemcpyAsync(params_out, c->d_out, (dim + 1) * sizeof(double), cudaMemcpyDefault, c->stream));
   if (pop_out)
-    PT_CUDA(c, cudaMemcpyAsync(pop_out, c->d_pop, (size_t)pop * D * sizeof(double), cudaMemcpyDefault, c->stream));
+    PT_CUDA(c, cudaMemcpyAsync(pop_out, c->d_pop, (size_t)pop * dim * sizeof(double), cudaMemcpyDefault, c->stream));
   if (fit_out)
     PT_CUDA(c, cudaMemcpyAsync(fit_out, c->d_fit, (size_t)pop * sizeof(double), cudaMemcpyDefault, c->stream));
   PT_CUDA(c, cudaStreamSynchronize(c->stream));
   return PT_OK;
+}
+
+// The full model runs the default tier, the chi-square and DE/rand/1/bin only.
+int check_full_settings(pt_ctx* c) {
+  if (c->objective != PT_OBJ_CHI2)
+    return fail(c, PT_EINVAL, "the full model runs on the chi-square objective only");
+  if (c->strategy != PT_DE_RAND1_BIN) return fail(c, PT_EINVAL, "the full model runs DE/rand/1/bin only");
+  return PT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int tier) {
+  if (!c) return PT_EINVAL;
+  return objective_impl(c, cands, n, sse_out, tier, MODEL_CUBIC);
+}
+
+int pt_objective_full(pt_ctx* c, const double* cands, int64_t n, double* sse_out) {
+  if (!c) return PT_EINVAL;
+  const int rc = check_full_settings(c);
+  if (rc != PT_OK) return rc;
+  return objective_impl(c, cands, n, sse_out, PT_TIER_F64, MODEL_FULL);
+}
+
+int pt_de_solve_ex(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
+                   uint32_t block_id, double* params_out, double* pop_out, double* fit_out, int tier) {
+  if (!c) return PT_EINVAL;
+  return de_solve_impl(c, bounds, pop, gens, F, CR, seed, block_id, params_out, pop_out, fit_out, tier, MODEL_CUBIC);
+}
+
+int pt_de_solve_full(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
+                     uint32_t block_id, double* params_out, double* pop_out, double* fit_out) {
+  if (!c) return PT_EINVAL;
+  const int rc = check_full_settings(c);
+  if (rc != PT_OK) return rc;
+  return de_solve_impl(c, bounds, pop, gens, F, CR, seed, block_id, params_out, pop_out, fit_out, PT_TIER_F64,
+                       MODEL_FULL);
 }
 
 int pt_de_solve(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,

@@ -24,6 +24,14 @@ namespace pt {
 typedef unsigned __int128 u128;
 
 constexpr int D = 5;             // (A, phi0, f0, f1, f2)
+// The full model: Eq. 2-2-2 with the amplitude slope c5 (A1) and the phase of
+// Eq. 2-2-1 to order n = 4 (Sec. 3.2, arcs near perigee),
+//   m(t) = (A + A1 t) cos(2 pi p(t)),  p(t) = ... + f3 t^4 / 24,
+// parameters (A, phi0, f0, f1, f2, A1, f3).
+constexpr int DF = 7;
+constexpr int MODEL_CUBIC = 0;
+constexpr int MODEL_FULL = 1;
+__host__ __device__ constexpr int model_dim(int model) { return model == MODEL_FULL ? DF : D; }
 constexpr int M = 8;             // samples per lane per tile
 constexpr int L = 32 * M;        // samples per tile
 constexpr int NP_MAX = 128;      // largest population / candidate batch per CTA
@@ -54,6 +62,7 @@ struct BlockArgs {
   double t0, h;          // t_i = t0 + i h
   double t0sq_2, t0cu_6; // t0^2/2, t0^3/6
   double h2_2, h3_6;     // h^2/2, h^3/6
+  double t0qu_24, h4_24; // t0^4/24, h^4/24 (full model)
 };
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -133,7 +142,7 @@ constexpr int DE_BEST1_JITTER = 3;
 constexpr int DE_EITHER_OR = 6;
 
 struct DeControls {
-  double lo[D], hi[D];
+  double lo[DF], hi[DF];  // the first model_dim(model) entries are used
   double F;
   double K;          // (F + 1) / 2, for DE_EITHER_OR
   uint32_t cr_thr;   // crossover if word < cr_thr
@@ -144,12 +153,19 @@ struct DeControls {
   uint32_t block_id;
 };
 
-// Generation-0 individual: uniform inside the bounds.
+// Generation-0 individual: uniform inside the bounds; component j from words
+// 2j, 2j+1 (words 12, 13 from counter group 3 for the full model's last one).
+template <int DIM = D>
 __device__ __forceinline__ void de_init(const DeControls& dc, int i, double* xi) {
-  uint32_t w[12];
+  uint32_t w[14];
   de_draw12(dc.key, dc.block_id, 0u, (uint32_t)i, w);
+  if (DIM > 6) {
+    const uint4 g3 = philox4x32_10(make_uint4(3u, (uint32_t)i, 0u, dc.block_id), dc.key);
+    w[12] = g3.x;
+    w[13] = g3.y;
+  }
 #pragma unroll
-  for (int j = 0; j < D; ++j)
+  for (int j = 0; j < DIM; ++j)
     xi[j] = __dadd_rn(dc.lo[j], __dmul_rn(u53(w[2 * j], w[2 * j + 1]), __dsub_rn(dc.hi[j], dc.lo[j])));
 }
 
@@ -166,7 +182,7 @@ __device__ __forceinline__ long long dkey(double a) {
 // DE_EITHER_OR marks a three-point trial in bit 24 of rpack and takes every
 // component; DE_BEST1_JITTER also writes the five jitter words of the trial
 // (words 9..11, then words 0..1 of a fourth counter group) to jit[0..4].
-template <int STRAT>
+template <int STRAT, int DIM = D>
 __device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, uint32_t gen, uint32_t* rpack,
                                          uint32_t* take, uint32_t* jit) {
   uint32_t w[12];
@@ -197,15 +213,15 @@ __device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, ui
     excl[pos] = v;
     nex++;
   }
-  const uint32_t jrand = lemire(w[3], (uint32_t)D);
+  const uint32_t jrand = lemire(w[3], (uint32_t)DIM);
   uint32_t m = 0;
 #pragma unroll
-  for (int j = 0; j < D; ++j)
+  for (int j = 0; j < DIM; ++j)
     if ((uint32_t)j == jrand || dc.cr_all || w[4 + j] < dc.cr_thr) m |= 1u << j;
   *rpack = r[0] | (r[1] << 8) | (r[2] << 16);
   *take = m;
   if (STRAT == DE_EITHER_OR) {
-    *take = (1u << D) - 1u;
+    *take = (1u << DIM) - 1u;
     if (w[9] >= 0x80000000u) *rpack |= 1u << 24;
   }
 }
@@ -220,28 +236,28 @@ __device__ __forceinline__ double half_exact(double x) {
 }
 
 // Component j of the DE/rand/1/bin trial of individual i from population x
-// (np x 5). FP64 operations use _rn intrinsics so no contraction changes a
+// (np x DIM). FP64 operations use _rn intrinsics so no contraction changes a
 // rounding: the value is bit-identical to a plain IEEE evaluation.
 // STRAT is the DE_* strategy (a template parameter, so each strategy's loop
 // holds only its own FP64 operations); `best` (the previous generation's
 // lowest-index minimum) and jit (the trial's five jitter words) are used by
 // DE_BEST1_JITTER only.
-template <int STRAT>
+template <int STRAT, int DIM = D>
 __device__ __forceinline__ double de_component(const DeControls& dc, const double* x, int i, int j, uint32_t rpack,
                                                uint32_t take, int best, const uint32_t* jit) {
-  const double parent = x[i * D + j];
+  const double parent = x[i * DIM + j];
   if (!((take >> j) & 1u)) return parent;
   const int r0 = rpack & 0xff, r1 = (rpack >> 8) & 0xff, r2 = (rpack >> 16) & 0xff;
   double v;
   if (STRAT == DE_BEST1_JITTER) {
     const double Fj = __dadd_rn(dc.F, __dmul_rn(1e-4, (double)jit[j] * (1.0 / 4294967296.0)));
-    v = __dadd_rn(x[best * D + j], __dmul_rn(Fj, __dsub_rn(x[r1 * D + j], x[r2 * D + j])));
+    v = __dadd_rn(x[best * DIM + j], __dmul_rn(Fj, __dsub_rn(x[r1 * DIM + j], x[r2 * DIM + j])));
   } else if (STRAT == DE_EITHER_OR) {
-    const double a = x[r0 * D + j], b = x[r1 * D + j], c = x[r2 * D + j];
+    const double a = x[r0 * DIM + j], b = x[r1 * DIM + j], c = x[r2 * DIM + j];
     if (rpack >> 24) v = __dadd_rn(a, __dmul_rn(dc.K, __dsub_rn(__dadd_rn(b, c), 2.0 * a)));
     else v = __dadd_rn(a, __dmul_rn(dc.F, __dsub_rn(b, c)));
   } else {
-    v = __dadd_rn(x[r0 * D + j], __dmul_rn(dc.F, __dsub_rn(x[r1 * D + j], x[r2 * D + j])));
+    v = __dadd_rn(x[r0 * DIM + j], __dmul_rn(dc.F, __dsub_rn(x[r1 * DIM + j], x[r2 * DIM + j])));
   }
   if (j == 1 && dc.periodic) {
     const double d = __dsub_rn(v, dc.lo[j]);
@@ -354,6 +370,73 @@ __device__ __forceinline__ uint4 make_anchor(const Poly& P, uint64_t i0) {
   return make_uint4(U0, V, __float_as_uint(e2), __float_as_uint(e3));
 }
 
+// ---------------------------------------------------------------------------
+// Full model (7 parameters): the phase polynomial in the sample index gains
+// E4 i^4, and the amplitude is linear in the sample index.
+
+// Coefficient E_k (k = 0..4) of full-model candidate th for the block's time
+// base (the Taylor coefficients of p at t0, times h^k):
+//   E4 = f3 h^4/24,  E3 = (f2 + f3 t0) h^3/6,  E2 = (f1 + f2 t0 + f3 t0^2/2) h^2/2,
+//   E1 = (f0 + f1 t0 + f2 t0^2/2 + f3 t0^3/6) h,
+//   E0 = phi0/(2 pi) + f0 t0 + f1 t0^2/2 + f2 t0^3/6 + f3 t0^4/24.
+__device__ __forceinline__ double poly_coef_full(const double* th, const BlockArgs& b, int k) {
+  const double phi0 = th[1], f0 = th[2], f1 = th[3], f2 = th[4], f3 = th[6];
+  if (k == 4) return f3 * b.h4_24;
+  if (k == 3) return fma(f3, b.t0, f2) * b.h3_6;
+  if (k == 2) return fma(f3, b.t0sq_2, fma(f2, b.t0, f1)) * b.h2_2;
+  if (k == 1) return fma(f3, b.t0cu_6, fma(f2, b.t0sq_2, fma(f1, b.t0, f0))) * b.h;
+  return fma(f3, b.t0qu_24, fma(f2, b.t0cu_6, fma(f1, b.t0sq_2, fma(f0, b.t0, phi0 * INV_TWO_PI))));
+}
+
+// The full model's amplitude A + A1 t at sample i as A0 + i a1h (FP32):
+// A0 = A + A1 t0, a1h = A1 h.
+struct AmpTerms {
+  float A0, a1h;
+};
+__device__ __forceinline__ AmpTerms full_amp(const double* th, double t0, double h) {
+  return {__double2float_rn(fma(th[5], t0, th[0])), __double2float_rn(th[5] * h)};
+}
+
+// Inside a lane's run of M samples kc + m' (|m'| <= M/2) the full model's
+// small phase terms are the Taylor expansion S0 + S1 m' + S2 m'^2 + S3 m'^3 +
+// S4 m'^4 about kc. Dropping S3 m'^3 + S4 m'^4 errs by at most
+// 2 pi ((M/2)^3 |S3| + (M/2)^4 |S4|) rad, with |S4| = |E4| and, the anchors
+// sitting at tile centres (i0 + L/2 <= n + L) and |kc| <= L/2,
+// |S3| <= |E3| + 4 |E4| (n + 2 L); a candidate keeps them when that bound
+// exceeds 2^-24 rad (NaN keeps them too).
+__device__ __forceinline__ bool quartic_needed(double E3, double E4, int64_t n) {
+  const double h = 0.5 * M;
+  const double s3 = fabs(E3) + 4.0 * fabs(E4) * (double)(n + 2 * L);
+  const double bound = TWO_PI * (h * h * h * s3 + h * h * h * h * fabs(E4));
+  return !(bound <= 5.9604644775390625e-08);
+}
+
+// Full-model tile anchor for samples i0 + k, i0 the tile's centre sample
+// (k in [-L/2, L/2)): exact mod 2^128,
+//   p(i0 + k) = P + D1 k + D2 k^2 + D3 k^3 + E4 k^4,
+//   P  = E0 + i0 (E1 + i0 (E2 + i0 (E3 + i0 E4))),
+//   D1 = E1 + i0 (2 E2 + i0 (3 E3 + 4 i0 E4)),
+//   D2 = E2 + i0 (3 E3 + 6 i0 E4),  D3 = E3 + 4 i0 E4;
+// first word (U0, V, 2 pi D2, 2 pi D3) as in make_anchor, second
+// (2 pi E4, amplitude at i0, a1h, 0).
+__device__ __forceinline__ void make_anchor_full(const u128 (&e)[5], uint64_t i0, float A0, float a1h, uint4* out) {
+  const u128 e4i = mul_u128_u64(e[4], i0);
+  const u128 e3x3 = e[3] + (e[3] << 1);
+  const u128 Pp = e[0] + mul_u128_u64(e[1] + mul_u128_u64(e[2] + mul_u128_u64(e[3] + e4i, i0), i0), i0);
+  const u128 D1 = e[1] + mul_u128_u64((e[2] << 1) + mul_u128_u64(e3x3 + (e4i << 2), i0), i0);
+  const u128 D2 = e[2] + mul_u128_u64(e3x3 + (e4i << 2) + (e4i << 1), i0);
+  const u128 D3 = e[3] + (e4i << 2);
+  const u128 half = ((u128)1) << 95;
+  const uint32_t U0 = (uint32_t)((Pp + half) >> 96);
+  const uint32_t V = (uint32_t)((D1 + half) >> 96);
+  const float d2 = i64_to_f32((long long)(uint64_t)(D2 >> 64)) * TWO_PI_2M64;
+  const float d3 = i64_to_f32((long long)(uint64_t)(D3 >> 64)) * TWO_PI_2M64;
+  const float d4 = i64_to_f32((long long)(uint64_t)(e[4] >> 64)) * TWO_PI_2M64;
+  const float At = fmaf((float)i0, a1h, A0);
+  out[0] = make_uint4(U0, V, __float_as_uint(d2), __float_as_uint(d3));
+  out[1] = make_uint4(__float_as_uint(d4), __float_as_uint(At), __float_as_uint(a1h), 0u);
+}
+
 // Exponent k of the fixed-point SSE accumulator of a candidate: every
 // partial and the total are at most B = n (smax + |A|)^2, and k is chosen so
 // that B * 2^k < 2^(bits+1). Computed in FP32 with a factor-2 margin for
@@ -381,6 +464,11 @@ __device__ __forceinline__ double fixed_to_double(unsigned long long acc, int k)
 }
 
 __device__ __forceinline__ float exp2_int_f(int k) { return __int_as_float((k + 127) << 23); }
+
+// The full model's exponent: |A + A1 t| <= |A0| + |a1h| n over the block.
+__device__ __forceinline__ int full_scale_exp(AmpTerms a, int64_t n, float smax, int bits) {
+  return sse_scale_exp(n, smax, fabsf(a.A0) + fabsf(a.a1h) * (float)n, bits);
+}
 
 // Objectives (Sec. 2.2): the chi-square of Eq. 2-2-4 and the correlation
 // objective of Eq. 2-2-5 with the constant-amplitude model of Eq. 2-2-6,

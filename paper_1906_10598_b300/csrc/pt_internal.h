@@ -21,6 +21,8 @@ namespace pt {
 // needs to size buffers; the launchers below fill the real structs.
 constexpr int HOST_L = 256;      // samples per tile
 constexpr int HOST_D = 5;        // parameters per candidate
+constexpr int HOST_DMAX = 7;     // parameters per candidate of the full model
+constexpr int HOST_MODEL_CUBIC = 0, HOST_MODEL_FULL = 1;
 constexpr int HOST_NP_MAX = 128;
 constexpr int HOST_RING_STRIDE = 16;  // 64-bit words per candidate slot of the DE exchange ring
 // words of one group's DE exchange ring: 3 generations x HOST_NP_MAX candidates
@@ -41,13 +43,13 @@ struct HostBlock {
 // One DE problem as the host describes it to the grouped launcher.
 struct HostDeBlock {
   HostBlock blk;
-  double lo[HOST_D], hi[HOST_D];
+  double lo[HOST_DMAX], hi[HOST_DMAX];  // the model's first 5 or 7 used
   int pop = 0, gens = 0;
   double F = 0.7, CR = 0.9;
   uint64_t seed = 0;
   uint32_t block_id = 0;
-  double* out = nullptr;      // device [6]
-  double* pop_out = nullptr;  // device [pop*5] or null
+  double* out = nullptr;      // device [dim + 1]
+  double* pop_out = nullptr;  // device [pop*dim] or null
   double* fit_out = nullptr;  // device [pop] or null
 };
 
@@ -120,8 +122,9 @@ int pick_cg(int tier, int n);
 int load_samples(pt_ctx* c, cudaStream_t stream, const void* samples, int64_t n, int dtype, double scale, double fs,
                  double t0, void** dbuf, size_t* cap, unsigned long long* d_u64, HostBlock* hb);
 
-// Validate DE arguments (bounds host pointer, 5 x 2).
-int check_de_args(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, int tier);
+// Validate DE arguments (bounds host pointer, dim x 2).
+int check_de_args(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, int tier,
+                  int dim = HOST_D);
 
 // Launch the grouped persistent DE kernel: `ngroups` groups of `k` CTAs,
 // group q solving blocks sched[off[q] .. off[q+1]) of `blocks` (host array,
@@ -133,7 +136,7 @@ constexpr int DE_UPLOAD = 1;  // copy descriptors and schedule to d_desc_buf
 constexpr int DE_LAUNCH = 2;  // clear ring and error word, launch
 int launch_de_groups(pt_ctx* c, cudaStream_t stream, int tier, const HostDeBlock* blocks, int nblocks,
                      const int* sched, const int* off, int ngroups, int k, void* d_desc_buf,
-                     unsigned long long* ring, int* d_err, int mode);
+                     unsigned long long* ring, int* d_err, int mode, int model = HOST_MODEL_CUBIC);
 
 // max |stored sample| of n samples at dsamples into *d_slot (which must be
 // zeroed first) by the absmax kernel. Asynchronous.
@@ -146,6 +149,6 @@ int kernel_status(pt_ctx* c, cudaStream_t s, int* d_err);
 size_t de_desc_bytes(int nblocks, int ngroups);
 
 // Staged tiles per CTA for a launch whose CTAs own at most `want` tiles.
-int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want);
+int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want, int model = HOST_MODEL_CUBIC);
 
 }  // namespace pt

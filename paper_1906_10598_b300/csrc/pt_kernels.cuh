@@ -20,6 +20,11 @@ namespace pt {
 
 constexpr int NT = 512;        // threads per CTA of the objective / DE kernels
 constexpr int CAND_BYTES = 64; // per-candidate prepared data in shared memory
+// The full model's per-candidate data: E0..E4 (5 x 16 B), then A0 and a1h (FP32).
+constexpr int CAND_BYTES_FULL = 96;
+__host__ __device__ constexpr int cand_bytes(int model) { return model == MODEL_FULL ? CAND_BYTES_FULL : CAND_BYTES; }
+// 16-byte anchor words per candidate and tile
+__host__ __device__ constexpr int anchor_words(int model) { return model == MODEL_FULL ? 2 : 1; }
 
 enum Tier { TIER_F64 = 0, TIER_PLAIN = 1, TIER_DF32 = 2, TIER_F32 = 3 };
 
@@ -106,10 +111,34 @@ __device__ __forceinline__ void prep_zero(unsigned char* cdata, float* negA, int
 // over separate threads so the 1/64-rate FP64 work is spread across all
 // warps of the CTA, and flags in cub[c] the candidates whose cubic term must
 // stay exact (cubic_needed). Ends with __syncthreads().
-template <int TIER, int OBJ = OBJ_CHI2>
+// The full model (default tier, chi-square) spreads its five terms and the
+// amplitude/flag/exponent work the same way.
+template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs& b, unsigned char* cdata,
                          float* negA, int* kexp, unsigned char* cub, int kbits) {
-  if (TIER == TIER_F64) {
+  if constexpr (MODEL == MODEL_FULL) {
+    for (int t = threadIdx.x; t < 6 * npad; t += blockDim.x) {
+      const int k = t / npad, c = t - k * npad;
+      const double* th = cands + c * DF;
+      unsigned char* cd = cdata + c * CAND_BYTES_FULL;
+      if (k < 5) {
+        reinterpret_cast<u128*>(cd)[k] = frac128(c < nc ? poly_coef_full(th, b, k) : 0.0);
+      } else if (c < nc) {
+        const AmpTerms am = full_amp(th, b.t0, b.h);
+        reinterpret_cast<float*>(cd + 80)[0] = am.A0;
+        reinterpret_cast<float*>(cd + 80)[1] = am.a1h;
+        negA[c] = 0.f;
+        kexp[c] = full_scale_exp(am, b.n, b.smax_f, kbits);
+        cub[c] = quartic_needed(poly_coef_full(th, b, 3), poly_coef_full(th, b, 4), b.n) ? 1 : 0;
+      } else {
+        reinterpret_cast<float*>(cd + 80)[0] = 0.f;
+        reinterpret_cast<float*>(cd + 80)[1] = 0.f;
+        negA[c] = 0.f;
+        kexp[c] = 0;
+        cub[c] = 0;
+      }
+    }
+  } else if (TIER == TIER_F64) {
     for (int t = threadIdx.x; t < 5 * npad; t += blockDim.x) {
       const int k = t / npad, c = t - k * npad;
       if (k < 4) {
@@ -248,6 +277,71 @@ __device__ __forceinline__ void item_f64_mixed(const float (&s)[M], const uint4*
   }
 }
 
+// Full model, one candidate: anchor words a = (U0, V, 2 pi D2, 2 pi D3) and
+// q = (2 pi E4, amplitude at the tile's centre, a1h), anchored at the tile's
+// centre sample (so kc = lane M + M/2 - L/2 lies in [-L/2, L/2) and the small
+// terms stay a quarter of their size at the tile start). The lane's phase is
+// anchored at its centre sample kc in fixed point; the small terms
+// Q(k) = d2 k^2 + d3 k^3 + d4 k^4 follow from their Taylor expansion about kc,
+//   S0 = Q(kc), S1 = Q'(kc), S2 = Q''(kc)/2, S3 = d3 + 4 d4 kc, S4 = d4,
+// x = xc + m' Vc + m'^2 S2 [+ m'^3 S3 + m'^4 S4] with xc = 2 pi frac(U0 + kc V)
+// + S0 and Vc = 2 pi V + S1; QUARTIC keeps the bracket (quartic_needed). The
+// amplitude walks as A_c + m' a1h from the lane centre.
+template <bool QUARTIC, bool MASKED>
+__device__ __forceinline__ float cand_full(const float (&s)[M], uint4 a, uint4 q, int lane, int nvalid) {
+  const int kci = lane * M + M / 2 - L / 2;
+  const float kc = (float)kci, kc2 = kc * kc, kc3 = kc2 * kc;
+  const uint32_t V = a.y;
+  const float d2 = __uint_as_float(a.z), d3 = __uint_as_float(a.w), d4 = __uint_as_float(q.x);
+  const float S0 = fmaf(d4, kc2 * kc2, fmaf(d3, kc3, d2 * kc2));
+  const float S1 = fmaf(4.0f * d4, kc3, fmaf(3.0f * d3, kc2, 2.0f * d2 * kc));
+  const float S2 = fmaf(6.0f * d4, kc2, fmaf(3.0f * d3, kc, d2));
+  const float S3 = fmaf(4.0f * d4, kc, d3);
+  const float xc = fmaf((float)(int)(a.x + (uint32_t)kci * V), TWO_PI_2M32, S0);
+  const float Vc = fmaf((float)(int)V, TWO_PI_2M32, S1);
+  const float na1 = -__uint_as_float(q.z);
+  const float nAc = fmaf(kc, na1, -__uint_as_float(q.y));
+  float sum = 0.f;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float mp = (float)(m - M / 2);
+    float x = xc;
+    if (m != M / 2) {
+      x = QUARTIC ? fmaf(mp, Vc, fmaf(mp * mp, S2, fmaf(mp * mp * mp, S3, fmaf(mp * mp * mp * mp, d4, xc))))
+                  : fmaf(mp, Vc, fmaf(mp * mp, S2, xc));
+    }
+    const float cv = __cosf(x);
+    const float nA = (m == M / 2) ? nAc : fmaf(mp, na1, nAc);
+    float r = fmaf(nA, cv, s[m]);
+    if (MASKED) r = (lane * M + m < nvalid) ? r : 0.f;
+    sum = fmaf(r, r, sum);
+  }
+  return sum;
+}
+
+// Full-model items: every candidate exact and masked on the ragged last tile;
+// on full tiles the flagged candidates keep the quartic terms.
+template <int CGV>
+__device__ __forceinline__ void item_full_masked(const float (&s)[M], const uint4* anc_i, int lane, int nvalid,
+                                                 float (&acc)[CGV]) {
+#pragma unroll
+  for (int c = 0; c < CGV; ++c) acc[c] = cand_full<true, true>(s, anc_i[2 * c], anc_i[2 * c + 1], lane, nvalid);
+}
+template <int CGV>
+__device__ __forceinline__ void item_full_fold(const float (&s)[M], const uint4* anc_i, int lane, float (&acc)[CGV]) {
+#pragma unroll
+  for (int c = 0; c < CGV; ++c) acc[c] = cand_full<false, false>(s, anc_i[2 * c], anc_i[2 * c + 1], lane, L);
+}
+template <int CGV>
+__device__ __forceinline__ void item_full_mixed(const float (&s)[M], const uint4* anc_i, const unsigned char* flags,
+                                                int lane, float (&acc)[CGV]) {
+#pragma unroll
+  for (int c = 0; c < CGV; ++c) {
+    if (flags[c]) acc[c] = cand_full<true, false>(s, anc_i[2 * c], anc_i[2 * c + 1], lane, L);
+    else acc[c] = cand_full<false, false>(s, anc_i[2 * c], anc_i[2 * c + 1], lane, L);
+  }
+}
+
 // All-FP64 tier: Horner phase in seconds, reduction mod 1, FP64 cospi.
 template <int CGV, bool MASKED>
 __device__ __forceinline__ void item_plain(const double (&s)[M], const unsigned char* cdata_g, int lane, int nvalid,
@@ -375,7 +469,7 @@ __device__ __forceinline__ bool any_flag(const unsigned char* f) {
 // the default tier each warp computes the tile anchors of its next IPB items
 // itself into its own slice of `anc` (IPB * CGV entries per warp), so no
 // CTA-wide barrier separates anchors from evaluation. Ends with __syncthreads().
-template <int TIER, int CGV, int OBJ = OBJ_CHI2>
+template <int TIER, int CGV, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, int item_hi, const float* s32,
                            const double* s64, const unsigned char* cdata, const float* negA, const int* kexp,
                            const unsigned char* cub, int ncand, int npad, uint4* anc, unsigned long long* acc) {
@@ -384,11 +478,31 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
   const int nitems = item_hi;
   const dfloat t0d = df_from_double(b.t0), hd = df_from_double(b.h);
   const float t0f = __double2float_rn(b.t0), hf = __double2float_rn(b.h);
-  uint4* anc_w = anc + warp * (IPB * CGV);
+  constexpr int AW = anchor_words(MODEL);
+  uint4* anc_w = anc + warp * (IPB * CGV * AW);
   constexpr int LPC = 32 / CGV;  // lanes holding each candidate's warp sum
 
   for (int base = item_lo + warp; base < nitems; base += nw * IPB) {
-    if (TIER == TIER_F64) {
+    if constexpr (MODEL == MODEL_FULL) {
+      for (int q = lane; q < IPB * CGV; q += 32) {
+        const int k = q / CGV, c = q - k * CGV;
+        const int it = base + k * nw;
+        uint4 av[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        if (it < nitems) {
+          const int t = it / G, cand = (it - t * G) * CGV + c;
+          if (cand < ncand) {
+            const unsigned char* cd = cdata + cand * CAND_BYTES_FULL;
+            const u128* e = reinterpret_cast<const u128*>(cd);
+            const u128 ev[5] = {e[0], e[1], e[2], e[3], e[4]};
+            const float* am = reinterpret_cast<const float*>(cd + 80);
+            make_anchor_full(ev, (uint64_t)(tile_begin + t) * (uint64_t)L + L / 2, am[0], am[1], av);
+          }
+        }
+        anc_w[2 * q] = av[0];
+        anc_w[2 * q + 1] = av[1];
+      }
+      __syncwarp();
+    } else if (TIER == TIER_F64) {
       for (int q = lane; q < IPB * CGV; q += 32) {
         const int k = q / CGV, c = q - k * CGV;
         const int it = base + k * nw;
@@ -449,7 +563,15 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
         float accv[CGV];
         const float* nA = negA + g * CGV;
         const unsigned char* cd = cdata + g * CGV * CAND_BYTES;
-        if (TIER == TIER_F64) {
+        if constexpr (MODEL == MODEL_FULL) {
+          const uint4* anc_i = anc_w + k * CGV * 2;
+          if (nvalid == L) {
+            if (any_flag<CGV>(cub + g * CGV)) item_full_mixed<CGV>(s, anc_i, cub + g * CGV, lane, accv);
+            else item_full_fold<CGV>(s, anc_i, lane, accv);
+          } else {
+            item_full_masked<CGV>(s, anc_i, lane, nvalid, accv);
+          }
+        } else if (TIER == TIER_F64) {
           const uint4* anc_i = anc_w + k * CGV;
           if (nvalid == L) {
             if (any_flag<CGV>(cub + g * CGV)) item_f64_mixed<CGV, OBJ>(s, anc_i, nA, cub + g * CGV, lane, accv);
@@ -507,16 +629,17 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 
 // npad: padded candidates; tmax: max tiles per CTA; cgv: candidates per item;
 // pop: population slots (0 for the objective kernel); nthreads: CTA size.
+// model: MODEL_CUBIC or MODEL_FULL (wider population rows, candidate data and anchors).
 __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, int cgv, int esize, int pop,
-                                                  int nthreads) {
+                                                  int nthreads, int model = MODEL_CUBIC) {
   SmemLayout s;
   size_t o = 0;
   s.off_mbar = o;
   o += 16;
   s.off_pop = o;
-  o += align_up((size_t)pop * (2 * D + 1) * sizeof(double), 16);
+  o += align_up((size_t)pop * (2 * model_dim(model) + 1) * sizeof(double), 16);
   s.off_cdata = o;
-  o += (size_t)npad * CAND_BYTES;
+  o += (size_t)npad * cand_bytes(model);
   s.off_negA = o;
   o += align_up((size_t)npad * sizeof(float), 16);
   s.off_kexp = o;
@@ -528,7 +651,7 @@ __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, 
   s.off_draw = o;
   o += align_up((size_t)(pop ? 7 * npad : 0) * sizeof(uint32_t), 16);  // rpack, take, 5 jitter words
   s.off_anc = o;
-  o += (tier == TIER_F64) ? (size_t)(nthreads / 32) * IPB * cgv * sizeof(uint4) : 0;
+  o += (tier == TIER_F64) ? (size_t)(nthreads / 32) * IPB * cgv * anchor_words(model) * sizeof(uint4) : 0;
   s.off_samp = o;
   o += align_up((size_t)tmax * L * (tier_uses_f64_samples(tier) ? 8 : 4), 128);
   s.off_raw = o;
@@ -558,7 +681,7 @@ struct ObjArgs {
   uint64_t timeout_ns;
 };
 
-template <int TIER, int CGV, int OBJ = OBJ_CHI2>
+template <int TIER, int CGV, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int64_t tb = (int64_t)blockIdx.x * a.tpc;
@@ -567,7 +690,7 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   const int nc = min(a.cpc, a.ncand - cb);
   if (nt <= 0 || nc <= 0) return;
   const int npad = (nc + CGV - 1) / CGV * CGV;
-  const SmemLayout S = smem_layout(TIER, npad, a.tpc, CGV, a.b.esize, 0, NT);
+  const SmemLayout S = smem_layout(TIER, npad, a.tpc, CGV, a.b.esize, 0, NT, MODEL);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S.off_mbar);
   unsigned char* cdata = smem + S.off_cdata;
   float* negA = reinterpret_cast<float*>(smem + S.off_negA);
@@ -581,19 +704,27 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
 
   const int tid = threadIdx.x;
   if (tid < npad) acc[tid] = 0ull;
-  prep_all<TIER, OBJ>(a.cands + (int64_t)cb * D, nc, npad, a.b, cdata, negA, kexp, cub,
-                      OBJ == OBJ_COR ? COR_BITS_OBJ : SSE_BITS_OBJ);
+  prep_all<TIER, OBJ, MODEL>(a.cands + (int64_t)cb * model_dim(MODEL), nc, npad, a.b, cdata, negA, kexp, cub,
+                             OBJ == OBJ_COR ? COR_BITS_OBJ : SSE_BITS_OBJ);
   if (!stage_tiles<TIER>(a.b, tb, nt, raw, s32, s64, mbar, a.timeout_ns, a.err)) return;
-  eval_range<TIER, CGV, OBJ>(a.b, tb, 0, nt * (npad / CGV), s32, s64, cdata, negA, kexp, cub, nc, npad, anc, acc);
+  eval_range<TIER, CGV, OBJ, MODEL>(a.b, tb, 0, nt * (npad / CGV), s32, s64, cdata, negA, kexp, cub, nc, npad, anc,
+                                    acc);
   if (tid < nc) atomicAdd(&a.acc[cb + tid], acc[tid]);
 }
 
 // The objective value of each candidate from its fixed-point sum: the SSE,
 // or for OBJ_COR F_cor from S = sum s_i cos(phi_i) and the candidate's A.
+// model MODEL_FULL: rows of 7 parameters, the full model's exponent (t0, h
+// give its amplitude terms).
 static __global__ void k_finalize(const double* cands, int ncand, const unsigned long long* acc, int64_t n, float smax_f,
-                                  double* sse, int obj) {
+                                  double* sse, int obj, int model, double t0, double h) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncand) return;
+  if (model == MODEL_FULL) {
+    const AmpTerms am = full_amp(cands + (int64_t)c * DF, t0, h);
+    sse[c] = fixed_to_double(acc[c], full_scale_exp(am, n, smax_f, SSE_BITS_OBJ));
+    return;
+  }
   const double A = cands[(int64_t)c * D];
   if (obj == OBJ_COR) {
     sse[c] = cor_objective_value(A, signed_fixed_to_double((long long)acc[c], cor_scale_exp(n, smax_f, COR_BITS_OBJ)));
@@ -608,8 +739,8 @@ struct DeBlockDesc {
   DeControls dc;
   int np, gens;
   int cg;            // candidates per work item for this block (16, 8 or 4)
-  double* out;       // [6] device: best params + SSE
-  double* pop_out;   // [np * 5] device or nullptr
+  double* out;       // [dim + 1] device: best params + SSE
+  double* pop_out;   // [np * dim] device or nullptr
   double* fit_out;   // [np] device or nullptr
 };
 
@@ -647,7 +778,7 @@ struct DeSmem {
 // DE_BEST1_JITTER mutates from the previous generation's lowest-index
 // minimum, which each thread finds itself (broadcast reads of the fitnesses,
 // no extra CTA barrier in the generation loop).
-template <int STRAT>
+template <int STRAT, int DIM = D>
 __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& sm, int np, int npad) {
   int best = 0;
   if (STRAT == DE_BEST1_JITTER) {
@@ -660,9 +791,10 @@ __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& s
       }
     }
   }
-  for (int t = threadIdx.x; t < D * npad; t += blockDim.x) {
+  for (int t = threadIdx.x; t < DIM * npad; t += blockDim.x) {
     const int j = t / npad, c = t - j * npad;
-    if (c < np) sm.u[c * D + j] = de_component<STRAT>(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c], best, sm.drj + c * D);
+    if (c < np)
+      sm.u[c * DIM + j] = de_component<STRAT, DIM>(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c], best, sm.drj + c * D);
   }
 }
 
@@ -675,9 +807,11 @@ __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& s
 // replaces a barrier, a fence and a separate read. `gg` counts the group's
 // generations across blocks so the ring discipline continues from block to
 // block. Returns false if a bounded wait expired or another CTA failed.
-template <int TIER, int CGV, int OBJ>
+// MODEL_FULL: the full model's 7 parameters (default tier, chi-square, DE/rand/1/bin).
+template <int TIER, int CGV, int OBJ, int MODEL = MODEL_CUBIC>
 __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long long* ring, unsigned long long& gg,
                          const DeSmem& sm, const DeLaunch& a, int* s_abort) {
+  constexpr int DIM = model_dim(MODEL);
   const int tid = threadIdx.x;
   const int np = d.np, npad = (d.np + CGV - 1) / CGV * CGV;
   const BlockArgs& b = d.b;
@@ -708,7 +842,9 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     }
     // trials u of this generation (the initial population at gen 0)
     if (gen == 0) {
-      if (tid < np) de_init(d.dc, tid, sm.u + tid * D);
+      if (tid < np) de_init<DIM>(d.dc, tid, sm.u + tid * DIM);
+    } else if constexpr (MODEL == MODEL_FULL) {
+      mutate_all<DE_RAND1_BIN, DIM>(d, sm, np, npad);
     } else {
       if (d.dc.strategy == DE_BEST1_JITTER) mutate_all<DE_BEST1_JITTER>(d, sm, np, npad);
       else if (d.dc.strategy == DE_EITHER_OR) mutate_all<DE_EITHER_OR>(d, sm, np, npad);
@@ -716,18 +852,18 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     }
     if (tid < npad) sm.acc[tid] = 0ull;
     __syncthreads();
-    prep_all<TIER, OBJ>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub,
-                        OBJ == OBJ_COR ? COR_BITS_DE : SSE_BITS_DE);
+    prep_all<TIER, OBJ, MODEL>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub,
+                               OBJ == OBJ_COR ? COR_BITS_DE : SSE_BITS_DE);
     if (resident) {
-      eval_range<TIER, CGV, OBJ>(b, tb, ilo, ihi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
-                                 sm.anc, sm.acc);
+      eval_range<TIER, CGV, OBJ, MODEL>(b, tb, ilo, ihi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
+                                        sm.anc, sm.acc);
     } else {
       for (int c0 = 0; c0 < nt; c0 += a.sc_tiles) {
         const int cn = min(a.sc_tiles, nt - c0);
         const int lo = max(ilo, c0 * G) - c0 * G, hi = min(ihi, (c0 + cn) * G) - c0 * G;
         if (!stage_tiles<TIER>(b, tb + c0, cn, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err)) return false;
-        eval_range<TIER, CGV, OBJ>(b, tb + c0, lo, hi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np,
-                                   npad, sm.anc, sm.acc);
+        eval_range<TIER, CGV, OBJ, MODEL>(b, tb + c0, lo, hi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub,
+                                          np, npad, sm.anc, sm.acc);
       }
     }
     if (tid < np) {
@@ -763,17 +899,19 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
       // with cor), so no FP64 arctangent sits on the generation's critical
       // path; F_cor is formed once for the outputs. dkey orders signed doubles.
       const double f = OBJ == OBJ_COR
-                           ? -(sm.u[tid * D] * signed_fixed_to_double((long long)v >> 8, sm.kexp[tid]))
+                           ? -(sm.u[tid * DIM] * signed_fixed_to_double((long long)v >> 8, sm.kexp[tid]))
                            : fixed_to_double(v >> 8, sm.kexp[tid]);
       if (gen == 0 || dkey(f) <= dkey(sm.fx[tid])) {
         sm.fx[tid] = f;
 #pragma unroll
-        for (int j = 0; j < D; ++j) sm.x[tid * D + j] = sm.u[tid * D + j];
+        for (int j = 0; j < DIM; ++j) sm.x[tid * DIM + j] = sm.u[tid * DIM + j];
       }
     } else if (gen < d.gens && tid >= NP_MAX && tid < NP_MAX + np) {
       // the next generation's draws do not depend on selection: overlap them with the wait
       const int c = tid - NP_MAX;
-      if (d.dc.strategy == DE_BEST1_JITTER)
+      if constexpr (MODEL == MODEL_FULL)
+        de_draws<DE_RAND1_BIN, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
+      else if (d.dc.strategy == DE_BEST1_JITTER)
         de_draws<DE_BEST1_JITTER>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
       else if (d.dc.strategy == DE_EITHER_OR)
         de_draws<DE_EITHER_OR>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
@@ -788,11 +926,11 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
       int best = 0;
       for (int i = 1; i < np; ++i)
         if (dkey(sm.fx[i]) < dkey(sm.fx[best])) best = i;
-      for (int j = 0; j < D; ++j) d.out[j] = sm.x[best * D + j];
-      d.out[D] = OBJ == OBJ_COR ? cor_objective_value(1.0, -sm.fx[best]) : sm.fx[best];
+      for (int j = 0; j < DIM; ++j) d.out[j] = sm.x[best * DIM + j];
+      d.out[DIM] = OBJ == OBJ_COR ? cor_objective_value(1.0, -sm.fx[best]) : sm.fx[best];
     }
     if (d.pop_out)
-      for (int i = tid; i < np * D; i += blockDim.x) d.pop_out[i] = sm.x[i];
+      for (int i = tid; i < np * DIM; i += blockDim.x) d.pop_out[i] = sm.x[i];
     if (d.fit_out)
       for (int i = tid; i < np; i += blockDim.x)
         d.fit_out[i] = OBJ == OBJ_COR ? cor_objective_value(1.0, -sm.fx[i]) : sm.fx[i];
@@ -804,15 +942,16 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
 // Persistent DE launch over groups of blocks (one block: one group of all CTAs).
 // Launched cooperatively: the k CTAs of a group wait on one another. OBJ
 // selects the objective every block of the launch minimises.
-template <int TIER, int OBJ = OBJ_CHI2>
+template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const SmemLayout S = smem_layout(TIER, NP_MAX, a.sc_tiles, 16, a.esize_max, NP_MAX, NT);
+  constexpr int DIM = model_dim(MODEL);
+  const SmemLayout S = smem_layout(TIER, NP_MAX, a.sc_tiles, 16, a.esize_max, NP_MAX, NT, MODEL);
   DeSmem sm;
   sm.mbar = reinterpret_cast<uint64_t*>(smem + S.off_mbar);
   sm.x = reinterpret_cast<double*>(smem + S.off_pop);
-  sm.u = sm.x + NP_MAX * D;
-  sm.fx = sm.u + NP_MAX * D;
+  sm.u = sm.x + NP_MAX * DIM;
+  sm.fx = sm.u + NP_MAX * DIM;
   sm.cdata = smem + S.off_cdata;
   sm.negA = reinterpret_cast<float*>(smem + S.off_negA);
   sm.kexp = reinterpret_cast<int*>(smem + S.off_kexp);
@@ -840,9 +979,9 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
     __syncthreads();
     const DeBlockDesc& d = s_desc;
     bool ok;
-    if (TIER == TIER_F64 && d.cg == 16) ok = de_block<TIER, 16, OBJ>(d, rank, a.k, ring, gg, sm, a, &s_abort);
-    else if (TIER == TIER_F64 && d.cg == 4) ok = de_block<TIER, 4, OBJ>(d, rank, a.k, ring, gg, sm, a, &s_abort);
-    else ok = de_block<TIER, 8, OBJ>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    if (TIER == TIER_F64 && d.cg == 16) ok = de_block<TIER, 16, OBJ, MODEL>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    else if (TIER == TIER_F64 && d.cg == 4) ok = de_block<TIER, 4, OBJ, MODEL>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    else ok = de_block<TIER, 8, OBJ, MODEL>(d, rank, a.k, ring, gg, sm, a, &s_abort);
     if (!ok) return;
   }
 }

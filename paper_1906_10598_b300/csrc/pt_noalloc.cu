@@ -151,7 +151,8 @@ extern "C" int pt_objective_noalloc(const void* samples, int64_t n, int dtype, d
   if (cudaMemsetAsync(scratch, 0, (NOALLOC_MAX_CANDS + 1) * sizeof(unsigned long long), s) != cudaSuccess)
     return PT_ECUDA;
   if ((rc = launch_any(tier, b, cands, (int)ncand, acc, err, s, sms, (size_t)optin)) != PT_OK) return rc;
-  k_finalize<<<(int)((ncand + 255) / 256), 256, 0, s>>>(cands, (int)ncand, acc, n, (float)smax, sse_out, OBJ_CHI2);
+  k_finalize<<<(int)((ncand + 255) / 256), 256, 0, s>>>(cands, (int)ncand, acc, n, (float)smax, sse_out, OBJ_CHI2,
+                                                       MODEL_CUBIC, 0.0, 1.0);
   if (cudaGetLastError() != cudaSuccess) return PT_ECUDA;
   int h_err = 0;
   if (cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -1,0 +1,171 @@
+"""GPU parity of the full model (amplitude slope c5, phase to order n = 4;
+Eq. 2-2-2 with Eq. 2-2-1 at n = 4, Sec. 3.2) against the oracle.
+
+* pt_objective_full matches oracle.sse_full within 1e-6 relative on blocks
+  with a ragged last tile, on candidates whose quartic terms fold and on
+  candidates that keep them (wide f2 / f3 ranges), and is bit-identical
+  across candidate batch sizes (item widths).
+* pt_de_solve_full reproduces the oracle's populations bit for bit in the
+  early generations, and its fit matches the oracle's (phi0 within 1e-3 rad,
+  f0 within 1e-5 Hz) on a perigee-shaped block.
+* Parameters held by equal bounds stay put; the entry points refuse the
+  correlation objective and the other strategies.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    build.build()
+    c = pt.Context(0)
+    yield c
+    c.close()
+
+
+def _cands_in(bounds, n, seed):
+    rng = np.random.default_rng(seed)
+    b = np.asarray(bounds)
+    return b[:, 0] + rng.random((n, b.shape[0])) * (b[:, 1] - b[:, 0])
+
+
+def _rel(g, o):
+    return np.abs(g - o) / np.maximum(np.abs(o), 1e-300)
+
+
+def _within(g, o, n, smax, amax):
+    """|dSSE| <= 1e-6 SSE + 2 sqrt(n SSE) dr + n dr^2: the relative target plus
+    the propagation of a per-sample FP32 residual error dr = 2e-6 (smax + |A|)
+    (SFU cosine ~4e-7, phase ~5e-7 rad, FP32 roundings of s and A; about a
+    factor 2 of margin), which dominates when a few samples leave a small SSE."""
+    dr = 2e-6 * (smax + amax)
+    return np.abs(g - o) <= 1e-6 * o + 2.0 * np.sqrt(n * o) * dr + n * dr * dr
+
+
+@pytest.mark.parametrize("n", [20_000, 257, 1])
+def test_objective_full_matches_oracle(ctx, n):
+    # the first n samples of a 2 s block (same time origin and windows)
+    blk = synth.perigee400k(1, n=20_000, storage=synth.I16)
+    samples = np.ascontiguousarray(blk.samples[:n])
+    ctx.load_block(samples, blk.fs, blk.t0, blk.scale)
+    cands = np.vstack([_cands_in(blk.bounds, 61, 2), blk.truth[None, :]])
+    g = ctx.objective_full(cands)
+    x = samples.astype(np.float64) * blk.scale
+    o = oracle.sse_full_many(x, blk.fs, blk.t0, cands)
+    if n >= 256:
+        assert np.all(_rel(g, o) <= 1e-6), float(np.max(_rel(g, o)))
+    tmax = max(abs(blk.t0), abs(blk.t0 + n / blk.fs))
+    amax = np.abs(cands[:, 0]) + np.abs(cands[:, 5]) * tmax
+    assert np.all(_within(g, o, n, np.max(np.abs(x)), amax)), np.abs(g - o)
+
+
+def test_objective_full_quartic_terms_kept(ctx):
+    # fs = 1 kHz, 3 s of a high-dynamics arc: at this rate f2 and f3 of a few
+    # Hz/s^2 and Hz/s^3 make the m'^3, m'^4 terms matter (quartic_needed);
+    # half the candidates have them negligible and fold
+    fs, n = 1000.0, 3000
+    truth = np.array([1.1, 0.4, 120.0, 1.0, 3.0, 0.03, 5.0])
+    t0 = synth.centred_t0(n, fs)
+    x = synth.clean_tone_full(truth, n, fs, t0) + np.random.default_rng(0).normal(0, 0.1, n)
+    ctx.load_block(x, fs, t0)
+    bounds = np.array([[0.9, 1.3], [-math.pi, math.pi], [119.0, 121.0], [-2.0, 2.0], [-6.0, 6.0],
+                       [-0.1, 0.1], [-8.0, 8.0]])
+    cands = _cands_in(bounds, 95, 3)
+    cands[::2, 4] *= 1e-2
+    cands[::2, 6] = 0.0
+    cands = np.vstack([cands, truth[None, :]])
+    g = ctx.objective_full(cands)
+    o = oracle.sse_full_many(x, fs, t0, cands)
+    assert np.all(_rel(g, o) <= 1e-6), float(np.max(_rel(g, o)))
+
+
+def test_objective_full_batch_shape_invariant(ctx):
+    blk = synth.perigee400k(2, n=30_000)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    cands = _cands_in(blk.bounds, 128, 4)
+    ref = ctx.objective_full(cands)
+    for m in (1, 4, 8, 16, 37, 100):
+        assert np.array_equal(ctx.objective_full(cands[:m]), ref[:m]), m
+
+
+def test_objective_full_reduces_to_cubic(ctx):
+    blk = synth.paper400k(3, n=20_000)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    c5 = _cands_in(blk.bounds, 40, 5)
+    c7 = np.hstack([c5, np.zeros((40, 2))])
+    g7 = ctx.objective_full(c7)
+    g5 = ctx.objective(c5)
+    o = oracle.sse_many(blk.values(), blk.fs, blk.t0, c5)
+    assert np.all(_rel(g7, o) <= 1e-6) and np.all(_rel(g5, o) <= 1e-6)
+
+
+def test_de_full_early_generations_bit_identical(ctx):
+    blk = synth.perigee400k(4, n=8192, storage=synth.F64)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    for gens, CR in ((0, 0.9), (1, 0.9), (6, 0.9), (6, 1.0)):
+        _, _, gpop, gfit = ctx.de_solve_full(blk.bounds, 32, gens, 0.7, CR, 91, block_id=3, return_population=True)
+        _, _, opop, ofit = oracle.de_solve_full(blk.values(), blk.fs, blk.t0, blk.bounds, 32, gens, 0.7, CR, 91,
+                                                block_id=3, return_population=True)
+        same = np.all(gpop == opop, axis=1)
+        assert same.sum() >= 31, (gens, CR, np.where(~same))
+        assert np.all(_rel(gfit[same], ofit[same]) <= 1e-6)
+
+
+def test_de_full_fit_matches_oracle(ctx):
+    blk = synth.perigee400k(5, n=20_000)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    g, gf = ctx.de_solve_full(blk.bounds, 48, 500, 0.7, 0.9, 13)
+    o, of = oracle.de_solve_full(blk.values(), blk.fs, blk.t0, blk.bounds, 48, 500, 0.7, 0.9, 13)
+    assert abs(math.remainder(g[1] - o[1], 2 * math.pi)) < 1e-3 and abs(g[2] - o[2]) < 1e-5
+    assert gf == pytest.approx(oracle.sse_full(blk.values(), blk.fs, blk.t0, g), rel=1e-6)
+    assert gf <= of * (1 + 1e-6)
+
+
+def test_de_full_paper_size_block_recovers_truth(ctx):
+    # N = 400,000 at 10 kHz (40 s): the quartic term moves the phase by cycles
+    # at the block edges; the fit reaches the noise floor and the truth
+    blk = synth.perigee400k(6, gens=1250)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    p, f = ctx.de_solve_full(blk.bounds, blk.pop, blk.gens, blk.F, blk.CR, blk.de_seed)
+    x = blk.values()
+    assert f <= oracle.sse_full(x, blk.fs, blk.t0, blk.truth) * (1 + 1e-6)
+    assert f == pytest.approx(oracle.sse_full(x, blk.fs, blk.t0, p), rel=1e-6)
+    assert abs(math.remainder(p[1] - blk.truth[1], 2 * math.pi)) < 0.05
+    assert abs(p[2] - blk.truth[2]) < 1e-3 and abs(p[6] - blk.truth[6]) < 1e-5
+
+
+def test_de_full_fixed_parameters_and_errors(ctx):
+    import paper_1906_10598_b300 as pt
+    blk = synth.perigee400k(7, n=6000)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    b = blk.bounds.copy()
+    b[5] = (0.0, 0.0)
+    b[6] = (blk.truth[6], blk.truth[6])
+    p, f, pop, fit = ctx.de_solve_full(b, 16, 20, 0.7, 0.9, 1, return_population=True)
+    assert np.all(pop[:, 5] == 0.0) and np.all(pop[:, 6] == blk.truth[6])
+    assert np.all(np.isfinite(fit)) and f == fit.min()
+    with pytest.raises(pt.PhaseTrackError):
+        ctx.de_solve_full(np.vstack([b[:6], [[1.0, 0.0]]]), 16, 5, 0.7, 0.9, 1)  # lo > hi
+    try:
+        ctx.set_objective("cor")
+        with pytest.raises(pt.PhaseTrackError):
+            ctx.objective_full(b[:, 0][None, :])
+        with pytest.raises(pt.PhaseTrackError):
+            ctx.de_solve_full(b, 16, 5, 0.7, 0.9, 1)
+    finally:
+        ctx.set_objective("chi2")
+    try:
+        ctx.set_strategy("best1jitter")
+        with pytest.raises(pt.PhaseTrackError):
+            ctx.de_solve_full(b, 16, 5, 0.7, 0.9, 1)
+    finally:
+        ctx.set_strategy("rand1bin")
