@@ -81,6 +81,9 @@ BlockArgs to_block_args(const HostBlock& h) {
   b.h3_6 = b.h * b.h * b.h / 6.0;
   b.t0qu_24 = h.t0 * h.t0 * h.t0 * h.t0 / 24.0;
   b.h4_24 = b.h * b.h * b.h * b.h / 24.0;
+  // quartic_needed: 2 pi ((M/2)^3 |S3| + (M/2)^4 |E4|), |S3| <= |E3| + 4 |E4| (n + 2 L), M/2 = 4
+  b.quartic_k3 = 2.0 * 3.14159265358979323846 * 64.0;
+  b.quartic_k4 = 2.0 * 3.14159265358979323846 * (256.0 + 4.0 * (double)(h.n + 2 * HOST_L) * 64.0);
   return b;
 }
 

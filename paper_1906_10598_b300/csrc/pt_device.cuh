@@ -63,6 +63,7 @@ struct BlockArgs {
   double t0sq_2, t0cu_6; // t0^2/2, t0^3/6
   double h2_2, h3_6;     // h^2/2, h^3/6
   double t0qu_24, h4_24; // t0^4/24, h^4/24 (full model)
+  double quartic_k3, quartic_k4;  // 2 pi (M/2)^3 and 2 pi ((M/2)^4 + 4 (n + 2 L) (M/2)^3), see quartic_needed
 };
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -403,11 +404,11 @@ __device__ __forceinline__ AmpTerms full_amp(const double* th, double t0, double
 // 2 pi ((M/2)^3 |S3| + (M/2)^4 |S4|) rad, with |S4| = |E4| and, the anchors
 // sitting at tile centres (i0 + L/2 <= n + L) and |kc| <= L/2,
 // |S3| <= |E3| + 4 |E4| (n + 2 L); a candidate keeps them when that bound
-// exceeds 2^-24 rad (NaN keeps them too).
-__device__ __forceinline__ bool quartic_needed(double E3, double E4, int64_t n) {
-  const double h = 0.5 * M;
-  const double s3 = fabs(E3) + 4.0 * fabs(E4) * (double)(n + 2 * L);
-  const double bound = TWO_PI * (h * h * h * s3 + h * h * h * h * fabs(E4));
+// exceeds 2^-24 rad (NaN keeps them too). With the block's constants
+// quartic_k3 = 2 pi (M/2)^3 and quartic_k4 = 2 pi ((M/2)^4 + 4 (n + 2 L) (M/2)^3)
+// the bound is quartic_k3 |E3| + quartic_k4 |E4|: one multiply and one FMA.
+__device__ __forceinline__ bool quartic_needed(double E3, double E4, const BlockArgs& b) {
+  const double bound = fma(b.quartic_k4, fabs(E4), b.quartic_k3 * fabs(E3));
   return !(bound <= 5.9604644775390625e-08);
 }
 
@@ -418,7 +419,7 @@ __device__ __forceinline__ bool quartic_needed(double E3, double E4, int64_t n) 
 //   D1 = E1 + i0 (2 E2 + i0 (3 E3 + 4 i0 E4)),
 //   D2 = E2 + i0 (3 E3 + 6 i0 E4),  D3 = E3 + 4 i0 E4;
 // first word (U0, V, 2 pi D2, 2 pi D3) as in make_anchor, second
-// (2 pi E4, amplitude at i0, a1h, 0).
+// (2 pi E4, -amplitude at i0, -a1h, 0).
 __device__ __forceinline__ void make_anchor_full(const u128 (&e)[5], uint64_t i0, float A0, float a1h, uint4* out) {
   const u128 e4i = mul_u128_u64(e[4], i0);
   const u128 e3x3 = e[3] + (e[3] << 1);
@@ -432,9 +433,9 @@ __device__ __forceinline__ void make_anchor_full(const u128 (&e)[5], uint64_t i0
   const float d2 = i64_to_f32((long long)(uint64_t)(D2 >> 64)) * TWO_PI_2M64;
   const float d3 = i64_to_f32((long long)(uint64_t)(D3 >> 64)) * TWO_PI_2M64;
   const float d4 = i64_to_f32((long long)(uint64_t)(e[4] >> 64)) * TWO_PI_2M64;
-  const float At = fmaf((float)i0, a1h, A0);
+  const float nAt = -fmaf((float)i0, a1h, A0);
   out[0] = make_uint4(U0, V, __float_as_uint(d2), __float_as_uint(d3));
-  out[1] = make_uint4(__float_as_uint(d4), __float_as_uint(At), __float_as_uint(a1h), 0u);
+  out[1] = make_uint4(__float_as_uint(d4), __float_as_uint(nAt), __float_as_uint(-a1h), 0u);
 }
 
 // Exponent k of the fixed-point SSE accumulator of a candidate: every

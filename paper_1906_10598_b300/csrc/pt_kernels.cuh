@@ -121,21 +121,25 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
       const int k = t / npad, c = t - k * npad;
       const double* th = cands + c * DF;
       unsigned char* cd = cdata + c * CAND_BYTES_FULL;
-      if (k < 5) {
+      if (k < 4) {
         reinterpret_cast<u128*>(cd)[k] = frac128(c < nc ? poly_coef_full(th, b, k) : 0.0);
+      } else if (k == 4) {
+        // E4, and the quartic flag from E4 and a second copy of E3 (two FP64
+        // operations) on the same thread
+        const double E4 = c < nc ? poly_coef_full(th, b, 4) : 0.0;
+        reinterpret_cast<u128*>(cd)[4] = frac128(E4);
+        cub[c] = c < nc && quartic_needed(poly_coef_full(th, b, 3), E4, b) ? 1 : 0;
       } else if (c < nc) {
         const AmpTerms am = full_amp(th, b.t0, b.h);
         reinterpret_cast<float*>(cd + 80)[0] = am.A0;
         reinterpret_cast<float*>(cd + 80)[1] = am.a1h;
         negA[c] = 0.f;
         kexp[c] = full_scale_exp(am, b.n, b.smax_f, kbits);
-        cub[c] = quartic_needed(poly_coef_full(th, b, 3), poly_coef_full(th, b, 4), b.n) ? 1 : 0;
       } else {
         reinterpret_cast<float*>(cd + 80)[0] = 0.f;
         reinterpret_cast<float*>(cd + 80)[1] = 0.f;
         negA[c] = 0.f;
         kexp[c] = 0;
-        cub[c] = 0;
       }
     }
   } else if (TIER == TIER_F64) {
@@ -278,7 +282,7 @@ __device__ __forceinline__ void item_f64_mixed(const float (&s)[M], const uint4*
 }
 
 // Full model, one candidate: anchor words a = (U0, V, 2 pi D2, 2 pi D3) and
-// q = (2 pi E4, amplitude at the tile's centre, a1h), anchored at the tile's
+// q = (2 pi E4, -amplitude at the tile's centre, -a1h), anchored at the tile's
 // centre sample (so kc = lane M + M/2 - L/2 lies in [-L/2, L/2) and the small
 // terms stay a quarter of their size at the tile start). The lane's phase is
 // anchored at its centre sample kc in fixed point; the small terms
@@ -290,17 +294,19 @@ __device__ __forceinline__ void item_f64_mixed(const float (&s)[M], const uint4*
 template <bool QUARTIC, bool MASKED>
 __device__ __forceinline__ float cand_full(const float (&s)[M], uint4 a, uint4 q, int lane, int nvalid) {
   const int kci = lane * M + M / 2 - L / 2;
-  const float kc = (float)kci, kc2 = kc * kc, kc3 = kc2 * kc;
+  // the lane's weights (the same for every candidate, so computed once per item)
+  const float kc = (float)kci, kc2 = kc * kc, kc3 = kc2 * kc, kc4 = kc2 * kc2;
   const uint32_t V = a.y;
   const float d2 = __uint_as_float(a.z), d3 = __uint_as_float(a.w), d4 = __uint_as_float(q.x);
-  const float S0 = fmaf(d4, kc2 * kc2, fmaf(d3, kc3, d2 * kc2));
-  const float S1 = fmaf(4.0f * d4, kc3, fmaf(3.0f * d3, kc2, 2.0f * d2 * kc));
-  const float S2 = fmaf(6.0f * d4, kc2, fmaf(3.0f * d3, kc, d2));
-  const float S3 = fmaf(4.0f * d4, kc, d3);
+  const float S0 = fmaf(kc4, d4, fmaf(kc3, d3, kc2 * d2));
+  const float S1 = fmaf(4.0f * kc3, d4, fmaf(3.0f * kc2, d3, (2.0f * kc) * d2));
+  const float S2 = fmaf(6.0f * kc2, d4, fmaf(3.0f * kc, d3, d2));
+  const float S3 = fmaf(4.0f * kc, d4, d3);
   const float xc = fmaf((float)(int)(a.x + (uint32_t)kci * V), TWO_PI_2M32, S0);
   const float Vc = fmaf((float)(int)V, TWO_PI_2M32, S1);
-  const float na1 = -__uint_as_float(q.z);
-  const float nAc = fmaf(kc, na1, -__uint_as_float(q.y));
+  // the anchor holds -A(tile centre) and -a1h
+  const float na1 = __uint_as_float(q.z);
+  const float nAc = fmaf(kc, na1, __uint_as_float(q.y));
   float sum = 0.f;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
