@@ -43,6 +43,7 @@ PAPER_SAMPLE_EVALS_PER_S = 400_000 * 80_000 / 6.5
 SMS, SFU_PER_CLK, SM_MAX_MHZ = 148, 16, 2032.0
 # ncu summary of the DE kernel: its DRAM bytes per launch and the sources it was taken on
 PROFILE = os.path.join(ROOT, "profiles", "k_de_paper400k_full.md")
+PROFILE_FULL_MODEL = os.path.join(ROOT, "profiles", "k_de_perigee400k_full_model.md")
 KERNEL_SOURCES = ("pt_kernels.cuh", "pt_device.cuh")
 
 
@@ -55,12 +56,12 @@ def kernel_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def profiled_traffic():
+def profiled_traffic(path: str = PROFILE):
     """(DRAM bytes per launch, note) from the committed ncu summary, or (None,
     why) when the kernel sources changed since that capture."""
     try:
         fields = {}
-        with open(PROFILE) as fh:
+        with open(path) as fh:
             for line in fh:
                 if ":" in line and line.startswith(("traffic_bytes_per_launch", "kernel_sources_sha256")):
                     k, v = line.split(":", 1)
@@ -68,7 +69,7 @@ def profiled_traffic():
         if fields.get("kernel_sources_sha256") != kernel_sources_sha256():
             return None, "kernel sources changed since the ncu capture"
         return int(fields["traffic_bytes_per_launch"]), "ncu dram__bytes_read + write, one launch (" + \
-            os.path.basename(PROFILE) + ")"
+            os.path.basename(path) + ")"
     except (OSError, KeyError, ValueError):
         return None, "no ncu summary"
 
@@ -256,10 +257,9 @@ def run_gpu(args):
     k_avg = float(np.mean(kern_ms)) * 1e-3
     achieved = evals / k_avg
     peak = SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6
-    traffic, traffic_note = profiled_traffic()
+    traffic, traffic_note = profiled_traffic(PROFILE_FULL_MODEL if full else PROFILE)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-            "traffic": None if full else traffic,
-            "traffic_note": "no ncu capture of the full-model kernel" if full else traffic_note,
+            "traffic": traffic, "traffic_note": traffic_note,
             "kernel": "k_de<TIER_F64, OBJ_CHI2, MODEL_FULL>" if full else "k_de<TIER_F64>",
             "peak_basis": "148 SMs x 16 SFU cosines/clk x 2032 MHz (one cosine per sample-eval)"}
     if clocks.get("sm_mhz"):
