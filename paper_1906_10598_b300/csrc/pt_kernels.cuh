@@ -838,13 +838,14 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
   for (int gen = 0; gen <= d.gens; ++gen, ++gg) {
     unsigned long long* slot = ring + (gg % 3) * (NP_MAX * RING_STRIDE);
     // the ring slot of the group's next generation was last read before the
-    // previous generation ended everywhere: rank 0 clears it (every word of the
-    // slot: the group's next block may have a larger population). No fence
-    // here: the CTA barriers below order the clears before rank 0's
-    // red.release contributions to this generation, a release is cumulative
-    // over writes ordered before it, and every reader acquires those
-    // contributions before it contributes to the next generation.
-    if (rank == 0 && tid < NP_MAX) ring[((gg + 1) % 3) * (NP_MAX * RING_STRIDE) + tid * RING_STRIDE] = 0ull;
+    // previous generation ended everywhere: rank 0 clears it, and its fence
+    // orders the clear before its own contributions to this generation, which
+    // every reader acquires before contributing to the next one
+    // (every word of the slot: the group's next block may have a larger population)
+    if (rank == 0 && tid < NP_MAX) {
+      ring[((gg + 1) % 3) * (NP_MAX * RING_STRIDE) + tid * RING_STRIDE] = 0ull;
+      __threadfence();
+    }
     // trials u of this generation (the initial population at gen 0)
     if (gen == 0) {
       if (tid < np) de_init<DIM>(d.dc, tid, sm.u + tid * DIM);
