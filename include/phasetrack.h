@@ -352,6 +352,24 @@ PT_API int pt_warm_bounds(const double prev[5], double dt, double T_next, double
 PT_API int pt_continuity(const double a[5], double Ta, const double b[5], double Tb, double max_dphi,
                          double max_dfreq, double* dphi, double* dfreq);
 
+/* Running-time ranges of the full model (7 parameters, see pt_de_solve_full)
+ * for block n+1 from block n's fit `prev`, as pt_warm_bounds with the phase
+ * carried to order 4: the f0, f1 and f2 ranges span the frequency
+ * f0 + f1 t + f2 t^2/2 + f3 t^3/6, its rate f1 + f2 t + f3 t^2/2 and
+ * f2 + f3 t over block n+1 (at least +-2/T, +-4/T^2, +-24/T^3 about their
+ * centre values), f3 +- 192/T^4 about prev's (about +-pi rad at the block
+ * edge, as f2's +-24/T^3 in the cubic model), A +- 10 % about the amplitude
+ * extrapolated to block n+1's centre, phi0 over the full circle, and A1 over
+ * a1_range (Sec. 3.1.1: "the range of c5 can be fixed"; NULL: prev's A1
+ * +- 0.2 A / T). bounds_out: 7 (lo, hi) pairs. Errors: PT_EINVAL. */
+PT_API int pt_warm_bounds_full(const double prev[7], double dt, double T_next, const double a1_range[2],
+                               double bounds_out[14]);
+
+/* pt_continuity for full-model fits: the border phase and frequency carry the
+ * f3 t^4/24 term. Returns 1, 0 or PT_EINVAL as pt_continuity. */
+PT_API int pt_continuity_full(const double a[7], double Ta, const double b[7], double Tb, double max_dphi,
+                              double max_dfreq, double* dphi, double* dfreq);
+
 /* ---- Block-to-block tracking of one stream ----------------------------------
  * The data process flow of Sec. 3.1.4 for one station stream cut into
  * contiguous blocks, each fitted about its own centre (t0 = -(n-1)/(2 fs)):
@@ -391,7 +409,8 @@ typedef struct pt_track_result {
   int64_t block_index;     /* 0, 1, ... in submission order */
   int quality;             /* accepted search (1..max_attempts), 0 = abandoned */
   int attempts;            /* searches made for this block */
-  double params[5];        /* accepted (A, phi0, f0, f1, f2) about the block centre; the last search's if abandoned */
+  double params[7];        /* accepted (A, phi0, f0, f1, f2, A1, f3) about the block centre; the last search's if
+                              abandoned; A1 = f3 = 0 in a cubic-model session */
   double sse;
   double dphi, dfreq;      /* continuity residuals of the accepted search (NaN if unchecked) */
   double phi_left, phi_right;  /* border phase mod 2 pi (rad) at -T/2 and T/2 */
@@ -405,6 +424,15 @@ typedef struct pt_track_result {
  * context at a time). bounds: the first block's (lo, hi) pairs for A, phi0,
  * f0, f1, f2 (host pointer, 10 doubles). Errors: PT_EINVAL, PT_ENOMEM. */
 PT_API int pt_track_create(pt_ctx* ctx, const pt_track_config* cfg, const double bounds[10], pt_track** out);
+
+/* A session that fits every block with the full model (pt_de_solve_full:
+ * amplitude slope and order-4 phase, for arcs near perigee, Sec. 3.2):
+ * bounds holds 7 (lo, hi) pairs; later blocks take pt_warm_bounds_full with
+ * the initial A1 range, acceptance uses pt_continuity_full, and a retry also
+ * widens the f3 range. cfg->tier is not used (the full model runs the default
+ * tier); the context must be on the chi-square and DE/rand/1/bin (the fits
+ * fail with PT_EINVAL otherwise). Errors: PT_EINVAL, PT_ENOMEM. */
+PT_API int pt_track_create_full(pt_ctx* ctx, const pt_track_config* cfg, const double bounds[14], pt_track** out);
 
 /* Fit the stream's next block (samples as in pt_load_block, the context's
  * current block is replaced), synchronously; *out is always written when the

@@ -372,6 +372,11 @@ def _serve_protos(lib):
     lib.pt_warm_bounds.restype = ctypes.c_int
     lib.pt_continuity.argtypes = [dp, ctypes.c_double, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
     lib.pt_continuity.restype = ctypes.c_int
+    lib.pt_warm_bounds_full.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp, dp]
+    lib.pt_warm_bounds_full.restype = ctypes.c_int
+    lib.pt_continuity_full.argtypes = [dp, ctypes.c_double, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       dp, dp]
+    lib.pt_continuity_full.restype = ctypes.c_int
     lib._serve_protos = True
 
 
@@ -406,6 +411,35 @@ def continuity(a, Ta: float, b, Tb: float, max_dphi: float, max_dfreq: float):
                            float(max_dfreq), ctypes.byref(dphi), ctypes.byref(dfreq))
     if rc < 0:
         raise PhaseTrackError(rc, "pt_continuity")
+    return bool(rc), dphi.value, dfreq.value
+
+
+def warm_bounds_full(prev, dt: float, T_next: float, a1_range=None):
+    """pt_warm_bounds_full: the full model's running-time ranges (7 x 2)."""
+    lib = load_library()
+    _serve_protos(lib)
+    p = _dvec(prev, 7)
+    out = np.zeros(14, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    a1 = None if a1_range is None else _dvec(a1_range, 2)
+    rc = lib.pt_warm_bounds_full(p.ctypes.data_as(dp), float(dt), float(T_next),
+                                 a1.ctypes.data_as(dp) if a1 is not None else None, out.ctypes.data_as(dp))
+    if rc != PT_OK:
+        raise PhaseTrackError(rc, "pt_warm_bounds_full")
+    return out.reshape(7, 2)
+
+
+def continuity_full(a, Ta: float, b, Tb: float, max_dphi: float, max_dfreq: float):
+    """pt_continuity_full: as ``continuity`` for full-model fits (7 parameters)."""
+    lib = load_library()
+    _serve_protos(lib)
+    av, bv = _dvec(a, 7), _dvec(b, 7)
+    dphi, dfreq = ctypes.c_double(), ctypes.c_double()
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib.pt_continuity_full(av.ctypes.data_as(dp), float(Ta), bv.ctypes.data_as(dp), float(Tb),
+                                float(max_dphi), float(max_dfreq), ctypes.byref(dphi), ctypes.byref(dfreq))
+    if rc < 0:
+        raise PhaseTrackError(rc, "pt_continuity_full")
     return bool(rc), dphi.value, dfreq.value
 
 
@@ -467,7 +501,7 @@ class TrackConfig(ctypes.Structure):
 class TrackResult(ctypes.Structure):
     """Mirror of ``pt_track_result``."""
     _fields_ = [("block_index", ctypes.c_int64), ("quality", ctypes.c_int), ("attempts", ctypes.c_int),
-                ("params", ctypes.c_double * 5), ("sse", ctypes.c_double), ("dphi", ctypes.c_double),
+                ("params", ctypes.c_double * 7), ("sse", ctypes.c_double), ("dphi", ctypes.c_double),
                 ("dfreq", ctypes.c_double), ("phi_left", ctypes.c_double), ("phi_right", ctypes.c_double),
                 ("f_left", ctypes.c_double), ("f_right", ctypes.c_double), ("total_phase", ctypes.c_double),
                 ("int_doppler", ctypes.c_double), ("interval_phase", ctypes.c_double)]
@@ -480,6 +514,8 @@ def _track_protos(lib):
     dp = ctypes.POINTER(ctypes.c_double)
     lib.pt_track_create.argtypes = [vp, ctypes.POINTER(TrackConfig), dp, ctypes.POINTER(vp)]
     lib.pt_track_create.restype = ctypes.c_int
+    lib.pt_track_create_full.argtypes = [vp, ctypes.POINTER(TrackConfig), dp, ctypes.POINTER(vp)]
+    lib.pt_track_create_full.restype = ctypes.c_int
     lib.pt_track_block.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(TrackResult)]
     lib.pt_track_block.restype = ctypes.c_int
@@ -492,7 +528,9 @@ class Tracker:
     """``pt_track``: block-to-block tracking of one stream on ``ctx`` (Sec. 3.1.4):
     warm-started ranges, the Eq. 3-1-2 continuity check, enlarge-and-retry up to
     ``max_attempts`` searches, and total phase / integration Doppler (Eq. 4-1-2).
-    ``block`` returns a dict of the ``pt_track_result`` fields."""
+    ``block`` returns a dict of the ``pt_track_result`` fields. With 7 x 2
+    bounds the session fits the full model (``pt_track_create_full``) and
+    ``params`` has 7 entries, else 5."""
 
     def __init__(self, ctx: Context, bounds, pop: int = 64, gens: int = 1250, F: float = 0.7, CR: float = 0.9,
                  seed: int = 0, tier: int = TIER_F64, max_dphi: float = 0.3, max_dfreq: float = 2 * np.pi * 1.0,
@@ -502,10 +540,14 @@ class Tracker:
         _track_protos(self._lib)
         c = TrackConfig(int(pop), int(gens), float(F), float(CR), int(seed), int(tier), float(max_dphi),
                         float(max_dfreq), float(enlarge), int(max_attempts), float(count_interval))
-        b = _dvec(bounds, 10)
+        b = np.ascontiguousarray(np.asarray(bounds, dtype=np.float64).reshape(-1))
+        if b.size not in (10, 14):
+            raise ValueError("Tracker bounds: 5 or 7 (lo, hi) pairs")
+        self._dim = b.size // 2
+        create = self._lib.pt_track_create_full if self._dim == 7 else self._lib.pt_track_create
         h = ctypes.c_void_p()
-        ctx._check(self._lib.pt_track_create(ctx.handle, ctypes.byref(c), b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                             ctypes.byref(h)))
+        ctx._check(create(ctx.handle, ctypes.byref(c), b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          ctypes.byref(h)))
         self._h = h
 
     def block(self, samples, fs: float, scale: float = 1.0) -> dict:
@@ -514,7 +556,7 @@ class Tracker:
         self._ctx._check(self._lib.pt_track_block(self._h, s.ctypes.data, s.size, _NP_TO_PT[s.dtype], float(scale),
                                                   float(fs), ctypes.byref(r)))
         out = {k: getattr(r, k) for k, _ in TrackResult._fields_}
-        out["params"] = np.array(list(r.params))
+        out["params"] = np.array(list(r.params)[:self._dim])
         return out
 
     def close(self):

@@ -373,6 +373,67 @@ int pt_warm_bounds(const double prev[5], double dt, double T_next, double min_f0
   return PT_OK;
 }
 
+int pt_warm_bounds_full(const double prev[7], double dt, double T_next, const double a1_range[2],
+                        double bounds_out[14]) {
+  if (!prev || !bounds_out || !(T_next > 0.0) || !std::isfinite(dt)) return PT_EINVAL;
+  for (int j = 0; j < 7; ++j)
+    if (!std::isfinite(prev[j])) return PT_EINVAL;
+  if (a1_range && (!std::isfinite(a1_range[0]) || !std::isfinite(a1_range[1]) || a1_range[0] > a1_range[1]))
+    return PT_EINVAL;
+  const double T = T_next;
+  const double min_f0 = 2.0 / T, min_f1 = 4.0 / (T * T), min_f2 = 24.0 / (T * T * T),
+               min_f3 = 192.0 / (T * T * T * T);
+  const double A = prev[0], f0 = prev[2], f1 = prev[3], f2 = prev[4], A1 = prev[5], f3 = prev[6];
+  // frequency (Hz), its rate and the rate's derivative of the quartic phase, extrapolated from block n
+  auto freq = [&](double t) { return f0 + f1 * t + f2 * t * t / 2.0 + f3 * t * t * t / 6.0; };
+  auto rate = [&](double t) { return f1 + f2 * t + f3 * t * t / 2.0; };
+  auto jerk = [&](double t) { return f2 + f3 * t; };
+  const double ta = dt - T / 2.0, tb = dt + T / 2.0;
+  auto span = [&](auto fn, double mw, double* lo, double* hi) {
+    const double c = fn(dt);
+    *lo = std::min(std::min(std::min(fn(ta), fn(tb)), c), c - mw);
+    *hi = std::max(std::max(std::max(fn(ta), fn(tb)), c), c + mw);
+  };
+  const double An = std::fabs(A + A1 * dt);  // the amplitude at block n+1's centre
+  bounds_out[0] = An * 0.9;
+  bounds_out[1] = An * 1.1;
+  bounds_out[2] = -3.14159265358979323846;
+  bounds_out[3] = 3.14159265358979323846;
+  span(freq, min_f0, &bounds_out[4], &bounds_out[5]);
+  span(rate, min_f1, &bounds_out[6], &bounds_out[7]);
+  span(jerk, min_f2, &bounds_out[8], &bounds_out[9]);
+  if (a1_range) {
+    bounds_out[10] = a1_range[0];
+    bounds_out[11] = a1_range[1];
+  } else {
+    bounds_out[10] = A1 - 0.2 * An / T;
+    bounds_out[11] = A1 + 0.2 * An / T;
+  }
+  bounds_out[12] = f3 - min_f3;
+  bounds_out[13] = f3 + min_f3;
+  return PT_OK;
+}
+
+int pt_continuity_full(const double a[7], double Ta, const double b[7], double Tb, double max_dphi,
+                       double max_dfreq, double* dphi, double* dfreq) {
+  if (!a || !b || !dphi || !dfreq || !(Ta > 0.0) || !(Tb > 0.0)) return PT_EINVAL;
+  const double TWO_PI = 2.0 * 3.14159265358979323846;
+  // Eq. 3-1-1 carried to order 4: phase (rad) and frequency (rad/s)
+  auto phase = [&](const double* th, double t) {
+    return th[1] + TWO_PI * (th[2] * t + th[3] * t * t / 2.0 + th[4] * t * t * t / 6.0 +
+                             th[6] * t * t * t * t / 24.0);
+  };
+  auto freq = [&](const double* th, double t) {
+    return TWO_PI * (th[2] + th[3] * t + th[4] * t * t / 2.0 + th[6] * t * t * t / 6.0);
+  };
+  double d = std::fmod(phase(a, Ta / 2.0) - phase(b, -Tb / 2.0), TWO_PI);
+  if (d > TWO_PI / 2.0) d -= TWO_PI;
+  if (d < -TWO_PI / 2.0) d += TWO_PI;
+  *dphi = std::fabs(d);
+  *dfreq = std::fabs(freq(a, Ta / 2.0) - freq(b, -Tb / 2.0));
+  return (*dphi <= max_dphi && *dfreq <= max_dfreq) ? 1 : 0;
+}
+
 int pt_continuity(const double a[5], double Ta, const double b[5], double Tb, double max_dphi, double max_dfreq,
                   double* dphi, double* dfreq) {
   if (!a || !b || !dphi || !dfreq || !(Ta > 0.0) || !(Tb > 0.0)) return PT_EINVAL;

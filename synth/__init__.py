@@ -248,7 +248,8 @@ def batch(seed: int = 0, nblocks: int = 256, n_lo: int = 50_000, n_hi: int = 1_0
 @dataclasses.dataclass
 class StreamSpec:
     """One simulated station stream with a continuous phase
-    phi(t) = phi0 + 2 pi (F0 t + F1 t^2/2 + F2 t^3/6 + F3 t^4/24 + a sin(2 pi t / P))."""
+    phi(t) = phi0 + 2 pi (F0 t + F1 t^2/2 + F2 t^3/6 + F3 t^4/24 + a sin(2 pi t / P))
+    and amplitude A + A1 t (A1 = 0 unless set)."""
     stream_id: int
     fs: float
     block_s: float
@@ -262,6 +263,7 @@ class StreamSpec:
     dop_a: float
     dop_p: float
     seed: int
+    A1: float = 0.0
 
 
 def make_streams(seed: int = 0, fs_list=(10_000.0, 20_000.0, 35_000.0, 50_000.0), block_range=(1.0, 10.0)):
@@ -296,6 +298,29 @@ def stream_taylor_truth(spec: StreamSpec, tc: float) -> np.ndarray:
     return np.array([spec.A, ph, p1, p2, p3])
 
 
+def stream_taylor_truth_full(spec: StreamSpec, tc: float) -> np.ndarray:
+    """The full model's truth (A, phi0, f0, f1, f2, A1, f3) of the stream
+    re-centred at tc: the cubic truth, the amplitude slope, and the fourth
+    derivative of the phase; the sinusoid leaves an order-5 remainder."""
+    w = 2 * math.pi / spec.dop_p
+    t = stream_taylor_truth(spec, tc)
+    p4 = spec.F3 + spec.dop_a * w ** 4 * math.sin(w * tc)
+    return np.array([spec.A + spec.A1 * tc, t[1], t[2], t[3], t[4], spec.A1, p4])
+
+
+def perigee_stream(seed: int = 0, fs: float = 2000.0, block_s: float = 10.0, snr_db: float = 25.0) -> StreamSpec:
+    """A high-dynamics stream for the full model: a quartic phase whose
+    t^4 term moves a 10 s block's edge phase by a few tenths of a radian
+    (F3 ~ 2e-3 cycles/s^4, fourth derivative ~1e-2 rad/s^4), an amplitude
+    slope of ~0.5 %/s, no sinusoid (the block truth is exact)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 9_000_011))
+    return StreamSpec(0, float(fs), float(block_s), float(rng.uniform(0.8, 1.2)), float(snr_db),
+                      float(rng.uniform(-math.pi, math.pi)), float(rng.uniform(-0.2, 0.2) * fs),
+                      float(rng.uniform(-2, 2)), float(rng.uniform(-0.05, 0.05)),
+                      float(rng.choice([-1.0, 1.0]) * rng.uniform(1.5e-3, 2.5e-3)), 0.0, 400.0,
+                      int(rng.integers(0, 2 ** 31)), A1=float(rng.uniform(0.003, 0.006)))
+
+
 def stream_block(spec: StreamSpec, index: int) -> Block:
     """Block ``index`` of a stream: samples over [index*T, (index+1)*T) stored int16,
     time origin at the block centre; bounds are the paper400k windows around the
@@ -308,9 +333,10 @@ def stream_block(spec: StreamSpec, index: int) -> Block:
     rng = np.random.Generator(np.random.PCG64(spec.seed * 100_003 + index))
     sigma = _sigma_for(spec.A, spec.snr_db)
     noise = rng.normal(0.0, sigma, n)
-    x = spec.A * np.cos(2 * math.pi * stream_phase_cycles(spec, t_abs)) + noise
+    amp = spec.A + spec.A1 * t_abs if spec.A1 else spec.A
+    x = amp * np.cos(2 * math.pi * stream_phase_cycles(spec, t_abs)) + noise
     truth = stream_taylor_truth(spec, tc)
-    stored, scale = quantise(x, spec.A + 6.0 * sigma, I16)
+    stored, scale = quantise(x, float(np.max(np.abs(amp))) + 6.0 * sigma, I16)
     bounds = paper_bounds(rng, truth, n / fs)
     return Block(stored, I16, scale, fs, centred_t0(n, fs), truth, sigma, spec.snr_db, bounds, pop=64,
                  gens=max(200, int(math.ceil(80_000 / 64))), F=0.7, CR=0.9, de_seed=spec.seed + index,

@@ -138,3 +138,78 @@ def test_chirp_jump_recovered_by_enlarged_ranges(ctx):
     assert abs(r1["params"][2] - truth1[2]) < 0.05 and abs(r1["params"][3] - truth1[3]) < 0.5
     assert r1["dphi"] <= 0.3
     tr.close()
+
+
+def _perigee_bounds(sp, seed=0):
+    # the first block's windows around its full-model truth (offset like synth's):
+    # A +- 20 %, phi0 the full circle, f0 +- 2/T, f1 +- 4/T^2, f2 +- 24/T^3,
+    # A1 over the paper's +- 0.2 A / T, f3 +- 192/T^4
+    b0 = synth.stream_block(sp, 0)
+    T = b0.T
+    t0 = synth.stream_taylor_truth_full(sp, (b0.n - 1) / 2 / sp.fs)
+    rng = np.random.default_rng(seed)
+
+    def win(v, h):
+        c = v + rng.uniform(-0.5, 0.5) * h
+        return (c - h, c + h)
+
+    return np.array([(0.8 * t0[0], 1.2 * t0[0]), (-math.pi, math.pi), win(t0[2], 2 / T), win(t0[3], 4 / T ** 2),
+                     win(t0[4], 24 / T ** 3), (-0.24 * t0[0] / T, 0.24 * t0[0] / T), win(t0[6], 192 / T ** 4)])
+
+
+def test_full_model_tracks_a_perigee_stream_the_cubic_model_cannot(ctx):
+    # Sec. 3.2: near perigee the fourth phase derivative cannot be ignored and
+    # the phase is taken to order n = 4. 10 s blocks at 2 kHz of a stream with
+    # F3 ~ 1.6e-3 cycles/s^4 and an amplitude slope.
+    import paper_1906_10598_b300 as pt
+    sp = synth.perigee_stream(0)
+    bounds = _perigee_bounds(sp)
+    nblk, per_interval = 7, 3
+    kw = dict(pop=64, gens=800, seed=1, max_dphi=0.05, max_dfreq=0.05, max_attempts=3)
+    full = pt.Tracker(ctx, bounds, count_interval=per_interval * sp.block_s, **kw)
+    cubic = pt.Tracker(ctx, bounds[:5], **kw)
+    q_cubic = []
+    for k in range(nblk):
+        b = synth.stream_block(sp, k)
+        tc = (k * b.n + (b.n - 1) / 2) / sp.fs
+        truth = synth.stream_taylor_truth_full(sp, tc)
+        r = full.block(b.samples, b.fs, b.scale)
+        assert r["quality"] == 1 and r["attempts"] == 1, (k, r["dphi"], r["dfreq"])
+        assert len(r["params"]) == 7
+        assert abs(r["params"][2] - truth[2]) < 1e-3 and abs(r["params"][6] - truth[6]) < 2e-4
+        assert abs(r["params"][5] - truth[5]) < 2e-3
+        # the fit reaches the noise floor (int16 quantisation adds ~1e-7 of it)
+        assert r["sse"] <= float(np.sum(b.noise ** 2)) * (1 + 1e-3)
+        if k:
+            assert r["dphi"] < 0.02 and r["dfreq"] < 0.02
+        if (k + 1) % per_interval == 0:
+            t_s = (k + 1 - per_interval) * b.n / sp.fs - 0.5 / sp.fs
+            t_e = (k + 1) * b.n / sp.fs - 0.5 / sp.fs
+            true_phase = 2 * math.pi * float(synth.stream_phase_cycles(sp, np.array([t_e]))[0]
+                                             - synth.stream_phase_cycles(sp, np.array([t_s]))[0])
+            assert abs(r["interval_phase"] - true_phase) < 0.02
+        q_cubic.append(cubic.block(b.samples, b.fs, b.scale)["quality"])
+    # the cubic model's border frequencies disagree by ~0.23 rad/s (the quartic
+    # term it cannot represent): its searches fail the check and blocks are abandoned
+    assert q_cubic[0] == 1 and sum(q == 0 for q in q_cubic[1:]) >= (nblk - 1) // 2, q_cubic
+    full.close()
+    cubic.close()
+
+
+def test_full_model_tracker_refuses_other_settings(ctx):
+    import paper_1906_10598_b300 as pt
+    sp = synth.perigee_stream(0)
+    bounds = _perigee_bounds(sp)
+    b = synth.stream_block(sp, 0)
+    tr = pt.Tracker(ctx, bounds, pop=16, gens=10)
+    try:
+        ctx.set_objective("cor")
+        with pytest.raises(pt.PhaseTrackError):
+            tr.block(b.samples, b.fs, b.scale)
+    finally:
+        ctx.set_objective("chi2")
+    r = tr.block(b.samples, b.fs, b.scale)
+    assert r["block_index"] == 0 and len(r["params"]) == 7
+    tr.close()
+    with pytest.raises(ValueError):
+        pt.Tracker(ctx, bounds[:6], pop=16, gens=10)

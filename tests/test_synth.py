@@ -56,3 +56,26 @@ def test_stream_taylor_truth_catches_a_wrong_coefficient():
         t2[j] += scale * (abs(t2[j]) + 1.0)
         model = t2[2] * tau + t2[3] * tau ** 2 / 2 + t2[4] * tau ** 3 / 6
         assert np.any(np.abs(p - model) > bound), j
+
+
+@pytest.mark.parametrize("index", [0, 2, 5])
+def test_stream_quartic_truth_within_lagrange_bound_eq_3_2_2(index):
+    # the full model's truth (order n = 4) against Eq. 3-2-2 with n = 4:
+    # |R_4(t)| <= max |phi^(5)| |t - tc|^5 / 5!, phi^(5) = a w^5 cos(w t) here
+    specs = synth.make_streams(seed=5) + [synth.perigee_stream(1)]
+    for spec in specs:
+        n = int(round(spec.block_s * spec.fs))
+        tc = (index * n + (n - 1) / 2.0) / spec.fs
+        tau = (np.arange(n, dtype=np.float64) - (n - 1) / 2.0) / spec.fs
+        th = synth.stream_taylor_truth_full(spec, tc)
+        p = synth.stream_phase_cycles(spec, tc + tau) - synth.stream_phase_cycles(spec, np.array([tc]))[0]
+        model = th[2] * tau + th[3] * tau ** 2 / 2 + th[4] * tau ** 3 / 6 + th[6] * tau ** 4 / 24
+        w = 2 * math.pi / spec.dop_p
+        bound = spec.dop_a * w ** 5 * np.abs(tau) ** 5 / 120.0
+        assert np.all(np.abs(p - model) <= bound * (1 + 1e-9) + 1e-8), spec.stream_id
+        # the amplitude at the centre and its slope
+        assert th[0] == pytest.approx(spec.A + spec.A1 * tc) and th[5] == spec.A1
+        # dropping the quartic term leaves the order-4 remainder f3 tau^4 / 24 (up to the bound)
+        if spec.F3 != 0.0 and spec.dop_a == 0.0:
+            cubic = model - th[6] * tau ** 4 / 24
+            assert np.max(np.abs(p - cubic)) == pytest.approx(abs(th[6]) * np.max(tau ** 4) / 24, rel=1e-6)

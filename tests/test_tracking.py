@@ -67,3 +67,48 @@ def test_warm_bounds_rejects_bad_input(pt):
         pt.warm_bounds([1, 0, 0, 0, np.nan], 1.0, 1.0)
     with pytest.raises(pt.PhaseTrackError):
         pt.warm_bounds([1, 0, 0, 0, 0], 1.0, 0.0)
+
+
+def test_continuity_full_matches_oracle_quartic_phase(pt):
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        a = np.array([1.0, rng.uniform(-3, 3), rng.uniform(-200, 200), rng.uniform(-5, 5), rng.uniform(-0.5, 0.5),
+                      rng.uniform(-0.01, 0.01), rng.uniform(-0.01, 0.01)])
+        b = a + rng.normal(0, [0, 0.01, 1e-3, 1e-3, 1e-4, 0, 1e-5])
+        Ta, Tb = rng.uniform(1, 10), rng.uniform(1, 10)
+        ok, dphi, dfreq = pt.continuity_full(a, Ta, b, Tb, 0.05, 0.5)
+        pa = 2 * np.pi * oracle.phase_cycles_full(a, Ta / 2)
+        pb = 2 * np.pi * oracle.phase_cycles_full(b, -Tb / 2)
+        assert dphi == pytest.approx(abs(np.angle(np.exp(1j * (pa - pb)))), abs=1e-6)
+        # frequency: the oracle's phase derivative by a central difference
+        h = 1e-4
+        fa = 2 * np.pi * (oracle.phase_cycles_full(a, Ta / 2 + h) - oracle.phase_cycles_full(a, Ta / 2 - h)) / (2 * h)
+        fb = 2 * np.pi * (oracle.phase_cycles_full(b, -Tb / 2 + h) - oracle.phase_cycles_full(b, -Tb / 2 - h)) / (2 * h)
+        assert dfreq == pytest.approx(abs(fa - fb), abs=1e-4)
+        # with A1 = f3 = 0 it is the cubic check
+        a5, b5 = a.copy(), b.copy()
+        a5[5:] = 0.0
+        b5[5:] = 0.0
+        r7 = pt.continuity_full(a5, Ta, b5, Tb, 0.05, 0.5)
+        r5 = pt.continuity(a5[:5], Ta, b5[:5], Tb, 0.05, 0.5)
+        assert r7[0] == r5[0] and r7[1] == pytest.approx(r5[1], abs=1e-9) and r7[2] == pytest.approx(r5[2], rel=1e-12)
+
+
+def test_warm_bounds_full_contain_next_block_truth(pt):
+    specs = synth.make_streams(3) + [synth.perigee_stream(s) for s in range(3)]
+    for spec in specs:
+        T = spec.block_s
+        a1 = (spec.A1 - 0.2 * spec.A / T, spec.A1 + 0.2 * spec.A / T)
+        for k in range(4):
+            tc = (k + 0.5) * T
+            prev = synth.stream_taylor_truth_full(spec, tc)
+            nxt = synth.stream_taylor_truth_full(spec, tc + T)
+            b = pt.warm_bounds_full(prev, T, T, a1)
+            assert b[1, 0] == pytest.approx(-np.pi) and b[1, 1] == pytest.approx(np.pi)
+            for j in (0, 2, 3, 4, 5, 6):
+                assert b[j, 0] <= nxt[j] <= b[j, 1], (spec.stream_id, k, j, b[j], nxt[j])
+            assert tuple(b[5]) == a1
+    with pytest.raises(pt.PhaseTrackError):
+        pt.warm_bounds_full(np.full(7, np.nan), 1.0, 1.0)
+    with pytest.raises(pt.PhaseTrackError):
+        pt.warm_bounds_full(np.ones(7), 1.0, 1.0, (1.0, 0.0))
