@@ -331,3 +331,77 @@ def crb(theta, n: int, fs: float, t0: float, sigma: float) -> np.ndarray:
     g = np.stack([c, -A * s, -A * s * 2 * np.pi * t, -A * s * np.pi * t * t, -A * s * np.pi * t ** 3 / 3.0])
     J = (g @ g.T) / (sigma * sigma)
     return np.sqrt(np.diag(np.linalg.inv(J)))
+
+
+# ---------------------------------------------------------------------------
+# Initial ranges of the first block from FFTs (Sec. 3.1.1): the frequency at
+# the block centre from the spectrum of a small piece of data there, its rate
+# by a central difference of three such frequencies, the amplitude from the
+# spectral peak; ranges f0 and A +- 10 %, c3 in [-50, 50] rad/s^3, c5
+# +- 0.2 c4 / T. Readings (the paper gives no more): pieces of Np samples
+# (the largest power of two <= n/4, at most 8192), periodic Hann window,
+# positive frequencies only (a real tone cannot tell f0 from -f0), peak bin
+# refined by a parabola through the log magnitudes of the peak and its two
+# neighbours, each piece's frequency taken at its sample Np/2 (the window's
+# centre of symmetry), amplitude corrected by the window's response at the
+# refined offset.
+
+def seed_piece_len(n: int) -> int:
+    """Np: the largest power of two <= n/4, at most 8192 (0 if n < 64)."""
+    if n < 64:
+        return 0
+    return min(8192, 1 << int(np.floor(np.log2(n // 4))))
+
+
+def seed_pieces(samples, piece_len: int = 0):
+    """Refined peak of each of the three pieces: list of (start, bin, delta,
+    |X[bin]|) with the centre piece second. Piece k starts at n//2 - Np/2 +
+    (k - 1) Np."""
+    x = _f64(samples)
+    n = x.size
+    Np = piece_len or seed_piece_len(n)
+    if Np < 16 or Np & (Np - 1) or n // 2 - 3 * Np // 2 < 0 or n // 2 + 3 * Np // 2 > n:
+        raise ValueError("seed: block too short for three pieces")
+    w = 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(Np) / Np)
+    out = []
+    for k in range(3):
+        s = n // 2 - Np // 2 + (k - 1) * Np
+        X = np.fft.rfft(w * x[s:s + Np])
+        mag = np.abs(X)
+        kk = 1 + int(np.argmax(mag[1:Np // 2]))  # bins 1 .. Np/2 - 1, the first maximum
+        a, b, g = np.log(mag[kk - 1]), np.log(mag[kk]), np.log(mag[kk + 1])
+        den = a - 2.0 * b + g
+        delta = 0.5 * (a - g) / den if den < 0.0 else 0.0
+        out.append((s, kk, float(delta), float(mag[kk])))
+    return out
+
+
+def seed_bounds(samples, fs: float, t0: float, f0_rel: float = 0.1, piece_len: int = 0):
+    """The FFT seed of Sec. 3.1.1 for the block t_i = t0 + i/fs: a dict with
+    the estimates f0 (Hz at t = 0), f1 (Hz/s), A, the pieces' frequencies and
+    bounds (7 x 2: A, phi0, f0, f1, f2, A1, f3; the first 5 rows are the cubic
+    model's). f1's range is +- max(f0_rel |f1|, fs^2 / Np^2) (one bin over
+    the pieces' spacing; the paper gives none), f3's is +- 192 / T^4 about 0
+    (about +- pi rad at the block edge; the paper gives none)."""
+    x = _f64(samples)
+    n = x.size
+    Np = piece_len or seed_piece_len(n)
+    pieces = seed_pieces(x, Np)
+    w = 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(Np) / Np)
+    freqs, times = [], []
+    for s, kk, delta, _ in pieces:
+        freqs.append((kk + delta) * fs / Np)
+        times.append(t0 + (s + Np // 2) / fs)
+    f1 = (freqs[2] - freqs[0]) / (times[2] - times[0])
+    f0 = freqs[1] - f1 * times[1]
+    _, _, d1, m1 = pieces[1]
+    resp = np.sinc(d1) / (1.0 - d1 * d1)  # the Hann window's response at the refined offset
+    A = 2.0 * m1 / (np.sum(w) * resp)
+    T = n / fs
+    f2_max = 3.0 * 50.0 / np.pi  # c3 = pi f2 / 3 in [-50, 50] rad/s^3
+    hw1 = max(f0_rel * abs(f1), fs * fs / (Np * Np))
+    b = np.array([[(1.0 - f0_rel) * A, (1.0 + f0_rel) * A], [-np.pi, np.pi],
+                  [f0 - f0_rel * abs(f0), f0 + f0_rel * abs(f0)], [f1 - hw1, f1 + hw1], [-f2_max, f2_max],
+                  [-0.2 * A / T, 0.2 * A / T], [-192.0 / T ** 4, 192.0 / T ** 4]])
+    return {"f0": float(f0), "f1": float(f1), "A": float(A), "piece_freqs": freqs, "piece_times": times,
+            "piece_len": Np, "pieces": pieces, "bounds": b}
