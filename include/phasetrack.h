@@ -370,6 +370,37 @@ PT_API int pt_warm_bounds_full(const double prev[7], double dt, double T_next, c
 PT_API int pt_continuity_full(const double a[7], double Ta, const double b[7], double Tb, double max_dphi,
                               double max_dfreq, double* dphi, double* dfreq);
 
+/* ---- Initial ranges from FFTs ------------------------------------------------
+ * Sec. 3.1.1: the first block's ranges come from an FFT of a small piece of
+ * data at the block centre (c1 and c4), a central difference of three
+ * frequencies near the centre (c2), and fixed ranges for c3 and c5. Here:
+ * three pieces of piece_len samples (0: the largest power of two <= n/4, at
+ * most 8192) starting at n/2 - piece_len/2 + (k - 1) piece_len, k = 0, 1, 2;
+ * a periodic Hann window; the peak of |X|^2 over bins 1 .. piece_len/2 - 1
+ * (lowest index on ties; positive frequencies, as a real tone cannot tell f0
+ * from -f0), refined by a parabola through the log magnitudes of the peak and
+ * its neighbours; each piece's frequency taken at its sample piece_len/2. */
+typedef struct pt_seed_result {
+  double f0;               /* frequency at t = 0 (Hz), from the centre piece and f1 */
+  double f1;               /* frequency rate (Hz/s), central difference of the outer pieces */
+  double A;                /* amplitude from the centre piece's peak, corrected by the window's response */
+  int piece_len;
+  int peak_bin[3];         /* each piece's peak bin */
+  double peak_delta[3];    /* its refined offset (bins) */
+  double piece_freq[3];    /* (peak_bin + peak_delta) fs / piece_len (Hz) */
+  double piece_time[3];    /* time of each piece's sample piece_len/2 (s) */
+  double bounds[14];       /* 7 (lo, hi) pairs: A, phi0, f0, f1, f2, A1, f3 (the first 5: the cubic model) */
+} pt_seed_result;
+
+/* Seed the loaded block's ranges: A and f0 +- f0_rel (the paper: 0.1) of their
+ * estimates, phi0 the full circle, f1 +- max(f0_rel |f1|, fs^2/piece_len^2)
+ * (the paper gives no f1 range: one bin over the pieces' spacing), f2 over
+ * c3 = pi f2 / 3 in [-50, 50] rad/s^3, A1 +- 0.2 A / T (T = n / fs) and f3
+ * +- 192 / T^4 (about +- pi rad at the block edge; the paper gives none).
+ * f0_rel in (0, 1), piece_len 0 or a power of two in [16, 8192] with three
+ * pieces inside the block. Errors: PT_EINVAL, PT_ENOBLOCK, PT_ECUDA. */
+PT_API int pt_seed_bounds(pt_ctx* ctx, double f0_rel, int piece_len, pt_seed_result* out);
+
 /* ---- Block-to-block tracking of one stream ----------------------------------
  * The data process flow of Sec. 3.1.4 for one station stream cut into
  * contiguous blocks, each fitted about its own centre (t0 = -(n-1)/(2 fs)):

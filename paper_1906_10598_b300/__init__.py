@@ -44,6 +44,14 @@ class PhaseTrackError(RuntimeError):
         self.code = code
 
 
+class SeedResult(ctypes.Structure):
+    """Mirror of ``pt_seed_result``."""
+    _fields_ = [("f0", ctypes.c_double), ("f1", ctypes.c_double), ("A", ctypes.c_double), ("piece_len", ctypes.c_int),
+                ("peak_bin", ctypes.c_int * 3), ("peak_delta", ctypes.c_double * 3),
+                ("piece_freq", ctypes.c_double * 3), ("piece_time", ctypes.c_double * 3),
+                ("bounds", ctypes.c_double * 14)]
+
+
 def load_library():
     """Load libphasetrack.so (raises if it has not been built)."""
     global _lib
@@ -83,6 +91,8 @@ def load_library():
     lib.pt_de_solve_full.restype = c_int
     lib.pt_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.pt_last_kernel_ms.restype = c_int
+    lib.pt_seed_bounds.argtypes = [vp, ctypes.c_double, c_int, ctypes.POINTER(SeedResult)]
+    lib.pt_seed_bounds.restype = c_int
     _lib = lib
     return lib
 
@@ -228,6 +238,15 @@ class Context:
         if return_population:
             return out[:7].copy(), float(out[7]), popv, fit
         return out[:7].copy(), float(out[7])
+
+    def seed_bounds(self, f0_rel: float = 0.1, piece_len: int = 0) -> dict:
+        """pt_seed_bounds: the FFT seed of the loaded block's ranges (Sec. 3.1.1);
+        ``bounds`` is 7 x 2 (its first 5 rows are the cubic model's)."""
+        r = SeedResult()
+        self._check(self._lib.pt_seed_bounds(self._h, float(f0_rel), int(piece_len), ctypes.byref(r)))
+        return {"f0": r.f0, "f1": r.f1, "A": r.A, "piece_len": r.piece_len, "peak_bin": list(r.peak_bin),
+                "peak_delta": list(r.peak_delta), "piece_freq": list(r.piece_freq),
+                "piece_time": list(r.piece_time), "bounds": np.array(list(r.bounds)).reshape(7, 2)}
 
     def last_kernel_ms(self) -> float:
         v = ctypes.c_float()

@@ -380,7 +380,7 @@ void pt_destroy(pt_ctx* c) {
   pt_serve_shutdown(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* bufs[] = {c->d_samples, c->d_acc, c->d_cands, c->d_sse, c->d_ring, c->d_err,
-                  c->d_out,     c->d_pop, c->d_fit,   c->d_u64, c->d_desc};
+                  c->d_out,     c->d_pop, c->d_fit,   c->d_u64, c->d_desc, c->d_seed};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);

@@ -82,6 +82,7 @@ struct pt_ctx {
   double* d_fit = nullptr;
   unsigned long long* d_u64 = nullptr;
   void* d_desc = nullptr;  // one block descriptor + a one-entry schedule
+  void* d_seed = nullptr;  // pt_seed_bounds: three peaks and the result
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   float last_ms = 0.f;
   uint64_t timeout_ns = 2000000000ull;
