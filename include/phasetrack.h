@@ -515,6 +515,20 @@ PT_API int pt_objective_noalloc(const void* samples, int64_t n, int dtype, doubl
  * work, measured with CUDA events on the context's stream. */
 PT_API int pt_last_kernel_ms(const pt_ctx* ctx, float* ms);
 
+/* Limit of every bounded device-side wait of this context's launches (the
+ * bulk-copy completion and the DE exchange's arrival polls), in seconds,
+ * 1e-3 .. 60 (default 2). A wait that runs out sets the launch's error word,
+ * every CTA returns, and the call reports PT_ETIMEOUT; the context stays
+ * usable. Errors: PT_EINVAL. */
+PT_API int pt_set_wait_timeout(pt_ctx* ctx, double seconds);
+
+/* Failure injection for tests of the bounded waits, host side: while enabled,
+ * the context's DE launches start one CTA fewer than the group size the
+ * kernel is told, so the last rank's arrivals never come and every
+ * exchange wait runs out after the wait limit (PT_ETIMEOUT). No fault, trap
+ * or unbounded wait is involved. Errors: PT_EINVAL. */
+PT_API int pt_inject_missing_cta(pt_ctx* ctx, int enable);
+
 #ifdef __cplusplus
 }
 #endif

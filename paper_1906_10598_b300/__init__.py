@@ -93,6 +93,10 @@ def load_library():
     lib.pt_last_kernel_ms.restype = c_int
     lib.pt_seed_bounds.argtypes = [vp, ctypes.c_double, c_int, ctypes.POINTER(SeedResult)]
     lib.pt_seed_bounds.restype = c_int
+    lib.pt_set_wait_timeout.argtypes = [vp, ctypes.c_double]
+    lib.pt_set_wait_timeout.restype = c_int
+    lib.pt_inject_missing_cta.argtypes = [vp, c_int]
+    lib.pt_inject_missing_cta.restype = c_int
     _lib = lib
     return lib
 
@@ -238,6 +242,15 @@ class Context:
         if return_population:
             return out[:7].copy(), float(out[7]), popv, fit
         return out[:7].copy(), float(out[7])
+
+    def set_wait_timeout(self, seconds: float):
+        """pt_set_wait_timeout: the limit of every bounded device-side wait."""
+        self._check(self._lib.pt_set_wait_timeout(self._h, float(seconds)))
+
+    def inject_missing_cta(self, enable: bool):
+        """pt_inject_missing_cta: DE launches start one CTA fewer than their
+        group (tests of the bounded waits; calls then fail with PT_ETIMEOUT)."""
+        self._check(self._lib.pt_inject_missing_cta(self._h, int(bool(enable))))
 
     def seed_bounds(self, f0_rel: float = 0.1, piece_len: int = 0) -> dict:
         """pt_seed_bounds: the FFT seed of the loaded block's ranges (Sec. 3.1.1);

@@ -158,7 +158,9 @@ int launch_de_t(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
   PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, OBJ, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, OBJ, MODEL>, NT, smem));
-  const int grid = a.ngroups * a.k;
+  // pt_inject_missing_cta: the last group's last rank is not started, so its
+  // arrivals never come and the others' bounded waits run out
+  const int grid = a.ngroups * a.k - (c->inject_missing_cta && a.ngroups * a.k > 1 ? 1 : 0);
   if (occ < 1 || grid > occ * c->sms) return fail(c, PT_EINVAL, "DE grid cannot be co-resident");
   void* args[] = {&a};
   PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, OBJ, MODEL>, dim3(grid), dim3(NT), args, smem, s));
@@ -396,6 +398,19 @@ int pt_set_strategy(pt_ctx* c, int strategy) {
   if (strategy != PT_DE_RAND1_BIN && strategy != PT_DE_BEST1_JITTER && strategy != PT_DE_EITHER_OR)
     return fail(c, PT_EINVAL, "unknown DE strategy");
   c->strategy = strategy;
+  return PT_OK;
+}
+
+int pt_set_wait_timeout(pt_ctx* c, double seconds) {
+  if (!c) return PT_EINVAL;
+  if (!(seconds >= 1e-3 && seconds <= 60.0)) return fail(c, PT_EINVAL, "pt_set_wait_timeout: 1e-3 .. 60 s");
+  c->timeout_ns = (uint64_t)(seconds * 1e9);
+  return PT_OK;
+}
+
+int pt_inject_missing_cta(pt_ctx* c, int enable) {
+  if (!c) return PT_EINVAL;
+  c->inject_missing_cta = enable != 0;
   return PT_OK;
 }
 

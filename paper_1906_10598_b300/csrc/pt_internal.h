@@ -86,6 +86,7 @@ struct pt_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   float last_ms = 0.f;
   uint64_t timeout_ns = 2000000000ull;
+  bool inject_missing_cta = false;  // pt_inject_missing_cta (tests of the bounded waits)
   int objective = 0;  // PT_OBJ_CHI2 or PT_OBJ_COR, for pt_objective and the DE entry points
   int strategy = 0;   // PT_DE_*, for the DE entry points
   // autotune cache of the batched launcher: per-CTA rate and per-generation costs
