@@ -91,7 +91,8 @@ typedef struct pt_ctx pt_ctx;
  *                A is each candidate's amplitude; a DE fit on PT_OBJ_COR
  *                should hold it constant (bounds lo = hi = the average
  *                amplitude), since a free A makes the objective divergent.
- *                Default tier only. */
+ *                Every tier (the sums are s_i cos(phi_i) in each tier's
+ *                arithmetic). */
 #define PT_OBJ_CHI2 0
 #define PT_OBJ_COR 1
 

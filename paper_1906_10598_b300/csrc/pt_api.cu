@@ -124,11 +124,17 @@ int launch_objective_any(pt_ctx* c, int tier, const double* d_cands, int ncand, 
     return launch_objective<TIER_F64, 4, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
   }
   if (c->objective == PT_OBJ_COR) {
-    if (tier != PT_TIER_F64) return fail(c, PT_EINVAL, "the correlation objective runs in the default tier only");
-    const int cg = pick_cg(tier, std::min(ncand, NP_MAX));
-    if (cg == 16) return launch_objective<TIER_F64, 16, OBJ_COR>(c, d_cands, ncand);
-    if (cg == 8) return launch_objective<TIER_F64, 8, OBJ_COR>(c, d_cands, ncand);
-    return launch_objective<TIER_F64, 4, OBJ_COR>(c, d_cands, ncand);
+    switch (tier) {
+      case PT_TIER_F64: {
+        const int cg = pick_cg(tier, std::min(ncand, NP_MAX));
+        if (cg == 16) return launch_objective<TIER_F64, 16, OBJ_COR>(c, d_cands, ncand);
+        if (cg == 8) return launch_objective<TIER_F64, 8, OBJ_COR>(c, d_cands, ncand);
+        return launch_objective<TIER_F64, 4, OBJ_COR>(c, d_cands, ncand);
+      }
+      case PT_TIER_PLAIN: return launch_objective<TIER_PLAIN, 8, OBJ_COR>(c, d_cands, ncand);
+      case PT_TIER_DF32: return launch_objective<TIER_DF32, 8, OBJ_COR>(c, d_cands, ncand);
+      default: return launch_objective<TIER_F32, 8, OBJ_COR>(c, d_cands, ncand);
+    }
   }
   switch (tier) {
     case PT_TIER_F64: {
@@ -303,8 +309,12 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   }
   a.obj = c->objective;
   if (a.obj == OBJ_COR) {
-    if (tier != PT_TIER_F64) return fail(c, PT_EINVAL, "the correlation objective runs in the default tier only");
-    return launch_de_t<TIER_F64, OBJ_COR>(c, s, a);
+    switch (tier) {
+      case PT_TIER_F64: return launch_de_t<TIER_F64, OBJ_COR>(c, s, a);
+      case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN, OBJ_COR>(c, s, a);
+      case PT_TIER_DF32: return launch_de_t<TIER_DF32, OBJ_COR>(c, s, a);
+      default: return launch_de_t<TIER_F32, OBJ_COR>(c, s, a);
+    }
   }
   switch (tier) {
     case PT_TIER_F64: return launch_de_t<TIER_F64>(c, s, a);

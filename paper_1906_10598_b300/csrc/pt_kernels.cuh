@@ -66,12 +66,12 @@ __device__ __forceinline__ dfloat df_from_double(double v) {
 //   TIER_PLAIN: double[5] = A, phi0/(2 pi), f0, f1/2, f2/6
 //   TIER_DF32:  dfloat[4] = c0..c3 (cycles, seconds), A in negA
 //   TIER_F32:   float[4]  = c0..c3
-template <int TIER>
+template <int TIER, int OBJ = OBJ_CHI2>
 __device__ __forceinline__ void prep_candidate(const double* th, const BlockArgs& b, unsigned char* cdata,
                                                float* negA, int* kexp, int kbits) {
   const float Af = __double2float_rn(th[0]);
   *negA = -Af;
-  *kexp = sse_scale_exp(b.n, b.smax_f, fabsf(Af), kbits);
+  *kexp = OBJ == OBJ_COR ? cor_scale_exp(b.n, b.smax_f, kbits) : sse_scale_exp(b.n, b.smax_f, fabsf(Af), kbits);
   if (TIER == TIER_F64) {
     u128* e = reinterpret_cast<u128*>(cdata);
 #pragma unroll
@@ -160,7 +160,7 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
     }
   } else {
     for (int c = threadIdx.x; c < npad; c += blockDim.x) {
-      if (c < nc) prep_candidate<TIER>(cands + c * D, b, cdata + c * CAND_BYTES, negA + c, kexp + c, kbits);
+      if (c < nc) prep_candidate<TIER, OBJ>(cands + c * D, b, cdata + c * CAND_BYTES, negA + c, kexp + c, kbits);
       else prep_zero(cdata + c * CAND_BYTES, negA + c, kexp + c);
     }
   }
@@ -349,7 +349,8 @@ __device__ __forceinline__ void item_full_mixed(const float (&s)[M], const uint4
 }
 
 // All-FP64 tier: Horner phase in seconds, reduction mod 1, FP64 cospi.
-template <int CGV, bool MASKED>
+// OBJ_COR accumulates s_i cos(phi_i) (the padding samples are zero).
+template <int CGV, bool MASKED, int OBJ = OBJ_CHI2>
 __device__ __forceinline__ void item_plain(const double (&s)[M], const unsigned char* cdata_g, int lane, int nvalid,
                                            int64_t tstart, const BlockArgs& b, double (&acc)[CGV]) {
 #pragma unroll 1
@@ -364,16 +365,20 @@ __device__ __forceinline__ void item_plain(const double (&s)[M], const unsigned 
       const double p = fma(fma(fma(c3, t, c2), t, c1), t, c0);
       const double r = p - rint(p);
       const double cv = cospi(2.0 * r);
-      double res = fma(-A, cv, s[m]);
-      if (MASKED) res = (lane * M + m < nvalid) ? res : 0.0;
-      sum = fma(res, res, sum);
+      if (OBJ == OBJ_COR) {
+        sum = fma(s[m], cv, sum);
+      } else {
+        double res = fma(-A, cv, s[m]);
+        if (MASKED) res = (lane * M + m < nvalid) ? res : 0.0;
+        sum = fma(res, res, sum);
+      }
     }
     acc[c] = sum;
   }
 }
 
 // Double-float tier: per-sample phase in double-float, FP32 cosine.
-template <int CGV, bool MASKED>
+template <int CGV, bool MASKED, int OBJ = OBJ_CHI2>
 __device__ __forceinline__ void item_df32(const float (&s)[M], const unsigned char* cdata_g, const float* negA_g,
                                           int lane, int nvalid, int64_t tstart, dfloat t0d, dfloat hd,
                                           float (&acc)[CGV]) {
@@ -394,16 +399,20 @@ __device__ __forceinline__ void item_df32(const float (&s)[M], const unsigned ch
       const float rh = p.hi - rintf(p.hi);
       const float r = rh + p.lo;
       const float cv = __cosf(r * 6.28318530717958648f);
-      float res = fmaf(nA, cv, s[m]);
-      if (MASKED) res = (lane * M + m < nvalid) ? res : 0.f;
-      sum = fmaf(res, res, sum);
+      if (OBJ == OBJ_COR) {
+        sum = fmaf(s[m], cv, sum);
+      } else {
+        float res = fmaf(nA, cv, s[m]);
+        if (MASKED) res = (lane * M + m < nvalid) ? res : 0.f;
+        sum = fmaf(res, res, sum);
+      }
     }
     acc[c] = sum;
   }
 }
 
 // Naive FP32 tier: Horner phase in seconds in FP32.
-template <int CGV, bool MASKED>
+template <int CGV, bool MASKED, int OBJ = OBJ_CHI2>
 __device__ __forceinline__ void item_f32(const float (&s)[M], const unsigned char* cdata_g, const float* negA_g,
                                          int lane, int nvalid, int64_t tstart, float t0f, float hf,
                                          float (&acc)[CGV]) {
@@ -420,9 +429,13 @@ __device__ __forceinline__ void item_f32(const float (&s)[M], const unsigned cha
       const float p = fmaf(fmaf(fmaf(c3, t, c2), t, c1), t, c0);
       const float r = p - rintf(p);
       const float cv = __cosf(r * 6.28318530717958648f);
-      float res = fmaf(nA, cv, s[m]);
-      if (MASKED) res = (lane * M + m < nvalid) ? res : 0.f;
-      sum = fmaf(res, res, sum);
+      if (OBJ == OBJ_COR) {
+        sum = fmaf(s[m], cv, sum);
+      } else {
+        float res = fmaf(nA, cv, s[m]);
+        if (MASKED) res = (lane * M + m < nvalid) ? res : 0.f;
+        sum = fmaf(res, res, sum);
+      }
     }
     acc[c] = sum;
   }
@@ -549,8 +562,8 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
           s[m + 1] = v.y;
         }
         double accv[CGV];
-        if (nvalid == L) item_plain<CGV, false>(s, cdata + g * CGV * CAND_BYTES, lane, nvalid, tstart, b, accv);
-        else item_plain<CGV, true>(s, cdata + g * CGV * CAND_BYTES, lane, nvalid, tstart, b, accv);
+        if (nvalid == L) item_plain<CGV, false, OBJ>(s, cdata + g * CGV * CAND_BYTES, lane, nvalid, tstart, b, accv);
+        else item_plain<CGV, true, OBJ>(s, cdata + g * CGV * CAND_BYTES, lane, nvalid, tstart, b, accv);
         const double z = warp_reduce_scatter<CGV>(accv, lane);
         if (owner) {
           const long long v = __double2ll_rn(z * __longlong_as_double((long long)(1023 + kexp[cand]) << 52));
@@ -586,11 +599,11 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
             item_f64<CGV, true, OBJ>(s, anc_i, nA, lane, nvalid, accv);
           }
         } else if (TIER == TIER_DF32) {
-          if (nvalid == L) item_df32<CGV, false>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
-          else item_df32<CGV, true>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
+          if (nvalid == L) item_df32<CGV, false, OBJ>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
+          else item_df32<CGV, true, OBJ>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
         } else {
-          if (nvalid == L) item_f32<CGV, false>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
-          else item_f32<CGV, true>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
+          if (nvalid == L) item_f32<CGV, false, OBJ>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
+          else item_f32<CGV, true, OBJ>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
         }
         const float z = warp_reduce_scatter<CGV>(accv, lane);
         if (owner) {

@@ -8,7 +8,10 @@ model of Eq. 2-2-6) against the FP64 oracle.
 * the per-candidate value is independent of the batch it is evaluated in
   (signed fixed-point sums);
 * DE on PT_OBJ_COR with A held constant reaches the oracle's fit within
-  1e-3 rad in phi0 and 1e-5 Hz in f0; the initial population is bit-identical.
+  1e-3 rad in phi0 and 1e-5 Hz in f0; the initial population is bit-identical;
+* the comparison tiers: the all-FP64 tier's cross-correlation within 1e-9 and
+  the double-float tier's within 2e-6 of n smax A, the all-FP64 tier's DE
+  populations bit-identical to the oracle's in the early generations.
 """
 import math
 
@@ -88,18 +91,48 @@ def test_cor_objective_independent_of_batch_shape(ctx):
         ctx.set_objective("chi2")
 
 
-def test_cor_default_tier_only(ctx):
+@pytest.mark.parametrize("tier,tol", [("plain", 1e-9), ("df32", 2e-6), ("f32", None)])
+def test_cor_comparison_tiers(ctx, tier, tol):
+    # the all-FP64 and double-float tiers against the oracle (cross-correlation
+    # relative to n smax A); the naive FP32 tier is reported, not bounded
     import paper_1906_10598_b300 as pt
-    blk = synth.paper400k(6, n=4096)
+    blk = synth.paper400k(11, n=50_000)
     ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
     ctx.set_objective("cor")
     try:
-        with pytest.raises(pt.PhaseTrackError):
-            ctx.objective(np.array([blk.truth]), pt.TIER_PLAIN)
+        A = float(blk.truth[0])
+        c = _cands(blk, np.random.default_rng(5), A)
+        got = ctx.objective(c, pt.TIERS[tier])
+        assert np.all(np.isfinite(got)) and np.all(got > 0)
+        if tol is None:
+            return
+        cor_g = np.tan(1.0 / got - math.pi / 2)
+        cor_o = np.array([oracle.cor(blk.values(), blk.fs, blk.t0, r) for r in c])
+        bound = blk.n * float(np.max(np.abs(blk.values()))) * A
+        sel = np.abs(cor_o) < 1e6
+        assert np.all(np.abs(cor_g[sel] - cor_o[sel]) <= tol * bound), np.max(np.abs(cor_g[sel] - cor_o[sel])) / bound
     finally:
         ctx.set_objective("chi2")
     with pytest.raises(pt.PhaseTrackError):
         ctx.set_objective(7)
+
+
+def test_cor_plain_tier_de_bit_identical(ctx):
+    import paper_1906_10598_b300 as pt
+    blk = synth.single4096(3)
+    b = blk.bounds.copy()
+    b[0] = (blk.truth[0], blk.truth[0])
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    ctx.set_objective("cor")
+    try:
+        for gens in (0, 1, 6):
+            _, _, gpop, gfit = ctx.de_solve(b, 32, gens, 0.7, 0.9, 17, pt.TIER_PLAIN, return_population=True)
+            _, _, opop, ofit = oracle.de_solve(blk.values(), blk.fs, blk.t0, b, 32, gens, 0.7, 0.9, 17,
+                                               return_population=True, objective="cor")
+            same = np.all(gpop == opop, axis=1)
+            assert same.sum() >= 31, (gens, np.where(~same))
+    finally:
+        ctx.set_objective("chi2")
 
 
 def test_cor_de_fit_matches_oracle(ctx):
