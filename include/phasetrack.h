@@ -272,11 +272,24 @@ typedef struct pt_batch_info {
 PT_API int pt_batch_create(pt_ctx* ctx, const pt_block_spec* specs, int nblocks, int tier, int group_ctas,
                            pt_batch** out);
 
+/* A batch of full-model fits (pt_de_solve_full: amplitude slope and order-4
+ * phase, default tier, chi-square, DE/rand/1/bin; PT_EINVAL otherwise):
+ * specs[i].bounds holds block i's first five (lo, hi) pairs and
+ * ext_bounds[4 i .. 4 i + 3] its A1 and f3 pairs (host pointer, nblocks x 4).
+ * The autotuner calibrates on the full model (its cache records the model).
+ * Results: pt_batch_results_full (pt_batch_results gives the first five). */
+PT_API int pt_batch_create_full(pt_ctx* ctx, const pt_block_spec* specs, const double* ext_bounds, int nblocks,
+                                int group_ctas, pt_batch** out);
+
 /* Solve every block of the batch (synchronous). Errors: PT_ECUDA, PT_ETIMEOUT. */
 PT_API int pt_batch_run(pt_batch* batch);
 
 /* Copy the results of the last run: out holds nblocks entries (host pointer). */
 PT_API int pt_batch_results(pt_batch* batch, pt_fit* out);
+
+/* The results of the last run as nblocks rows of 8 doubles (host pointer):
+ * (A, phi0, f0, f1, f2, A1, f3) and the SSE; A1 = f3 = 0 for a cubic batch. */
+PT_API int pt_batch_results_full(pt_batch* batch, double* out);
 
 PT_API int pt_batch_get_info(const pt_batch* batch, pt_batch_info* info);
 

@@ -303,6 +303,11 @@ def _batch_protos(lib):
     lib.pt_batch_run.restype = ctypes.c_int
     lib.pt_batch_results.argtypes = [vp, ctypes.POINTER(Fit)]
     lib.pt_batch_results.restype = ctypes.c_int
+    lib.pt_batch_create_full.argtypes = [vp, ctypes.POINTER(BlockSpec), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.pt_batch_create_full.restype = ctypes.c_int
+    lib.pt_batch_results_full.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.pt_batch_results_full.restype = ctypes.c_int
     lib.pt_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
     lib.pt_batch_get_info.restype = ctypes.c_int
     lib.pt_batch_destroy.argtypes = [vp]
@@ -314,8 +319,10 @@ class Batch:
     """``pt_batch``: many blocks solved by one persistent launch.
 
     ``blocks`` is a sequence of objects with ``samples`` (numpy), ``scale``,
-    ``fs``, ``t0``, ``bounds`` (5 x 2), ``pop``, ``gens``, ``F``, ``CR``,
-    ``de_seed`` and ``block_id`` attributes (e.g. ``synth.Block``)."""
+    ``fs``, ``t0``, ``bounds`` (5 x 2, or 7 x 2 for the full model), ``pop``,
+    ``gens``, ``F``, ``CR``, ``de_seed`` and ``block_id`` attributes (e.g.
+    ``synth.Block``). Blocks with 7 x 2 bounds make a full-model batch
+    (``pt_batch_create_full``; all blocks alike)."""
 
     def __init__(self, ctx: Context, blocks, tier: int = TIER_F64, group_ctas: int = 0):
         self._ctx = ctx
@@ -324,6 +331,11 @@ class Batch:
         n = len(blocks)
         specs = (BlockSpec * n)()
         keep = []
+        dims = {np.asarray(b.bounds).size // 2 for b in blocks}
+        if len(dims) != 1 or dims.pop() not in (5, 7):
+            raise ValueError("Batch: every block's bounds must be 5 x 2, or every block's 7 x 2")
+        self._dim = np.asarray(blocks[0].bounds).size // 2
+        ext = np.zeros((n, 4), dtype=np.float64)
         for i, b in enumerate(blocks):
             s = np.ascontiguousarray(b.samples)
             keep.append(s)
@@ -335,11 +347,19 @@ class Batch:
             bb = np.asarray(b.bounds, dtype=np.float64).reshape(-1)
             for j in range(10):
                 sp.bounds[j] = float(bb[j])
+            if self._dim == 7:
+                ext[i] = bb[10:14]
             sp.pop, sp.gens = int(b.pop), int(b.gens)
             sp.F, sp.CR = float(b.F), float(b.CR)
             sp.seed, sp.block_id = int(b.de_seed), int(b.block_id)
         self._h = ctypes.c_void_p()
-        ctx._check(self._lib.pt_batch_create(ctx.handle, specs, n, int(tier), int(group_ctas), ctypes.byref(self._h)))
+        if self._dim == 7:
+            ctx._check(self._lib.pt_batch_create_full(ctx.handle, specs,
+                                                      ext.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n,
+                                                      int(group_ctas), ctypes.byref(self._h)))
+        else:
+            ctx._check(self._lib.pt_batch_create(ctx.handle, specs, n, int(tier), int(group_ctas),
+                                                 ctypes.byref(self._h)))
         self.n = n
 
     def run(self) -> float:
@@ -348,12 +368,10 @@ class Batch:
         return self.info()["last_ms"]
 
     def results(self):
-        """(params[n, 5], sse[n]) of the last run."""
-        out = (Fit * self.n)()
-        self._ctx._check(self._lib.pt_batch_results(self._h, out))
-        params = np.array([list(f.params) for f in out])
-        sse = np.array([f.sse for f in out])
-        return params, sse
+        """(params[n, 5] or [n, 7] for the full model, sse[n]) of the last run."""
+        out = np.zeros((self.n, 8), dtype=np.float64)
+        self._ctx._check(self._lib.pt_batch_results_full(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out[:, :self._dim].copy(), out[:, 7].copy()
 
     def info(self) -> dict:
         i = BatchInfo()

@@ -29,13 +29,15 @@ using namespace pt;
 struct pt_batch {
   pt_ctx* ctx = nullptr;
   int tier = 0;
+  int model = HOST_MODEL_CUBIC;     // HOST_MODEL_FULL: pt_batch_create_full
+  int dim = HOST_D;                 // parameters per block fit
   int nblocks = 0;
   int ngroups = 0, k = 0;
   double predicted_ms = 0.0, sample_evals = 0.0;
   float last_ms = 0.f;
   void* d_arena = nullptr;          // all blocks' samples, each padded to a whole tile
   unsigned long long* d_amax = nullptr;
-  double* d_out = nullptr;          // nblocks x 6
+  double* d_out = nullptr;          // nblocks x (dim + 1)
   void* d_desc = nullptr;           // descriptors + schedule
   unsigned long long* d_ring = nullptr;
   int* d_err = nullptr;
@@ -52,7 +54,7 @@ int64_t padded_bytes(int64_t n, int esize) { return (n + HOST_L - 1) / HOST_L * 
 
 // Per-generation seconds of one DE run of `b` on k CTAs: time two runs that
 // differ only in the generation count and difference them.
-int time_per_gen(pt_ctx* c, int tier, HostDeBlock b, int k, double* out) {
+int time_per_gen(pt_ctx* c, int tier, HostDeBlock b, int k, int model, double* out) {
   const int sched[1] = {0}, off[2] = {0, 1};
   float ms[2];
   const int gens[2] = {4, 16};
@@ -63,7 +65,7 @@ int time_per_gen(pt_ctx* c, int tier, HostDeBlock b, int k, double* out) {
     b.fit_out = nullptr;
     PT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
     int rc = launch_de_groups(c, c->stream, tier, &b, 1, sched, off, 1, k, c->d_desc, c->d_ring, c->d_err,
-                              DE_UPLOAD | DE_LAUNCH);
+                              DE_UPLOAD | DE_LAUNCH, model);
     if (rc != PT_OK) return rc;
     PT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
     if ((rc = kernel_status(c, c->stream, c->d_err)) != PT_OK) return rc;
@@ -87,13 +89,14 @@ bool resident(const pt_ctx* c, int64_t ntiles, int k) { return (ntiles + k - 1) 
 
 int clamp_k(const pt_ctx* c, int64_t k) { return (int)std::max<int64_t>(1, std::min<int64_t>(k, c->sms)); }
 
-// Calibrate R_res, R_stream and c_gen (cached in the context).
-int calibrate(pt_ctx* c, int tier, const HostDeBlock& b0) {
-  if (c->tuned) return PT_OK;
+// Calibrate R_res, R_stream and c_gen (cached in the context for the model
+// they were measured on).
+int calibrate(pt_ctx* c, int tier, const HostDeBlock& b0, int model) {
+  if (c->tuned && c->tune_model == model) return PT_OK;
   const HostDeBlock& b = b0;
   const int64_t nt = b.blk.ntiles;
   const double np = (double)npad_of(tier, b.pop);
-  const int S = pick_sc_tiles(c, tier, b.blk.esize, 96);
+  const int S = pick_sc_tiles(c, tier, b.blk.esize, 96, model);
   c->tune_res_tiles = S;
   // two resident shapes: about S/3 and 2S/3 tiles per CTA
   int ka = clamp_k(c, (nt + std::max(1, S / 3) - 1) / std::max(1, S / 3));
@@ -102,9 +105,9 @@ int calibrate(pt_ctx* c, int tier, const HostDeBlock& b0) {
   double ta, tb;
   int rc;
   // the context's first DE launch also loads the module: run one untimed first
-  if ((rc = time_per_gen(c, tier, b, ka, &ta)) != PT_OK) return rc;
-  if ((rc = time_per_gen(c, tier, b, ka, &ta)) != PT_OK) return rc;
-  if ((rc = time_per_gen(c, tier, b, kb, &tb)) != PT_OK) return rc;
+  if ((rc = time_per_gen(c, tier, b, ka, model, &ta)) != PT_OK) return rc;
+  if ((rc = time_per_gen(c, tier, b, ka, model, &ta)) != PT_OK) return rc;
+  if ((rc = time_per_gen(c, tier, b, kb, model, &tb)) != PT_OK) return rc;
   const double wa = cta_samples(nt, ka), wb = cta_samples(nt, kb);
   const double R = (wb > wa && tb > ta) ? (wb - wa) * np / (tb - ta) : wa * np / ta;
   const double cg = std::max(0.0, ta - wa * np / R);
@@ -112,12 +115,13 @@ int calibrate(pt_ctx* c, int tier, const HostDeBlock& b0) {
   if (nt >= 3 * (int64_t)S) {
     const int ks = clamp_k(c, nt / (3 * (int64_t)S));
     double ts;
-    if ((rc = time_per_gen(c, tier, b, ks, &ts)) != PT_OK) return rc;
+    if ((rc = time_per_gen(c, tier, b, ks, model, &ts)) != PT_OK) return rc;
     if (ts > cg) Rs = cta_samples(nt, ks) * np / (ts - cg);
   }
   c->tune_rate = R;
   c->tune_rate_stream = Rs;
   c->tune_fixed_s = cg;
+  c->tune_model = model;
   c->tuned = true;
   return PT_OK;
 }
@@ -171,20 +175,27 @@ void release(pt_batch* b) {
   delete b;
 }
 
-}  // namespace
+// Block i's (lo, hi) pairs: the spec's five, then for the full model its
+// two rows of ext_bounds (A1, f3).
+void block_bounds(const pt_block_spec& s, const double* ext, int i, int dim, double* b) {
+  std::memcpy(b, s.bounds, sizeof(double) * 10);
+  if (dim == 7) std::memcpy(b + 10, ext + 4 * (size_t)i, sizeof(double) * 4);
+}
 
-extern "C" {
-
-int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier, int group_ctas, pt_batch** out) {
+int create_batch(pt_ctx* c, const pt_block_spec* specs, const double* ext_bounds, int nblocks, int tier,
+                 int group_ctas, int model, pt_batch** out) {
   if (!c) return PT_EINVAL;
-  if (!out || !specs || nblocks < 1 || !valid_tier(tier) || group_ctas < 0)
+  const int dim = model == HOST_MODEL_FULL ? HOST_DMAX : HOST_D;
+  if (!out || !specs || nblocks < 1 || !valid_tier(tier) || group_ctas < 0 || (dim == 7 && !ext_bounds))
     return fail(c, PT_EINVAL, "pt_batch_create: invalid argument");
   *out = nullptr;
   PT_CUDA(c, cudaSetDevice(c->device));
   int rc;
   for (int i = 0; i < nblocks; ++i) {
     const pt_block_spec& s = specs[i];
-    if ((rc = check_de_args(c, s.bounds, s.pop, s.gens, s.F, s.CR, tier)) != PT_OK) return rc;
+    double bnd[14];
+    block_bounds(s, ext_bounds, i, dim, bnd);
+    if ((rc = check_de_args(c, bnd, s.pop, s.gens, s.F, s.CR, tier, dim)) != PT_OK) return rc;
     if (!s.samples || s.n < 1 || esize_of(s.dtype) == 0 || !(s.scale > 0.0) || !(s.fs > 0.0) ||
         !std::isfinite(s.t0) || !std::isfinite(s.scale) || !std::isfinite(s.fs))
       return fail(c, PT_EINVAL, "pt_batch_create: invalid block " + std::to_string(i));
@@ -193,6 +204,8 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
   if (!b) return PT_ENOMEM;
   b->ctx = c;
   b->tier = tier;
+  b->model = model;
+  b->dim = dim;
   b->nblocks = nblocks;
   auto bail = [&](int code) {
     release(b);
@@ -208,7 +221,7 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
   cudaError_t e;
   if ((e = cudaMalloc(&b->d_arena, total)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_amax, nblocks * sizeof(unsigned long long))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_out, (size_t)nblocks * 6 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_out, (size_t)nblocks * (dim + 1) * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_err, sizeof(int))) != cudaSuccess || (e = cudaEventCreate(&b->ev0)) != cudaSuccess ||
       (e = cudaEventCreate(&b->ev1)) != cudaSuccess) {
     fail(c, e == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA,
@@ -246,9 +259,11 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
     h.blk.smax = a * sp.scale;
     h.blk.t0 = sp.t0;
     h.blk.fs = sp.fs;
-    for (int j = 0; j < HOST_D; ++j) {
-      h.lo[j] = sp.bounds[2 * j];
-      h.hi[j] = sp.bounds[2 * j + 1];
+    double bnd[14];
+    block_bounds(sp, ext_bounds, i, dim, bnd);
+    for (int j = 0; j < dim; ++j) {
+      h.lo[j] = bnd[2 * j];
+      h.hi[j] = bnd[2 * j + 1];
     }
     h.pop = sp.pop;
     h.gens = sp.gens;
@@ -256,11 +271,11 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
     h.CR = sp.CR;
     h.seed = sp.seed;
     h.block_id = sp.block_id;
-    h.out = b->d_out + (size_t)i * 6;
+    h.out = b->d_out + (size_t)i * (dim + 1);
     b->sample_evals += (double)sp.n * sp.pop * (sp.gens + 1);
   }
   // launch shape
-  if ((rc = calibrate(c, tier, b->blocks[0])) != PT_OK) return bail(rc);
+  if ((rc = calibrate(c, tier, b->blocks[0], model)) != PT_OK) return bail(rc);
   std::vector<int> ks;
   if (group_ctas > 0) ks.push_back(std::min(group_ctas, c->sms));
   else
@@ -289,7 +304,7 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
           cudaSuccess)
     return bail(fail(c, PT_ENOMEM, "pt_batch_create: descriptor allocation failed"));
   if ((rc = launch_de_groups(c, s, tier, b->blocks.data(), nblocks, b->sched.data(), b->off.data(), b->ngroups,
-                             b->k, b->d_desc, b->d_ring, b->d_err, DE_UPLOAD)) != PT_OK)
+                             b->k, b->d_desc, b->d_ring, b->d_err, DE_UPLOAD, model)) != PT_OK)
     return bail(rc);
   if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(c, PT_ECUDA, "pt_batch_create: upload failed"));
   // capture the launch (ring/error clears + cooperative kernel) as a graph;
@@ -299,7 +314,7 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
       const int lr = launch_de_groups(c, cs, tier, b->blocks.data(), nblocks, b->sched.data(), b->off.data(),
-                                      b->ngroups, b->k, b->d_desc, b->d_ring, b->d_err, DE_LAUNCH);
+                                      b->ngroups, b->k, b->d_desc, b->d_ring, b->d_err, DE_LAUNCH, model);
       cudaGraph_t g = nullptr;
       const cudaError_t ee = cudaStreamEndCapture(cs, &g);
       ok = lr == PT_OK && ee == cudaSuccess && g != nullptr;
@@ -318,6 +333,22 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
   return PT_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier, int group_ctas, pt_batch** out) {
+  return create_batch(c, specs, nullptr, nblocks, tier, group_ctas, HOST_MODEL_CUBIC, out);
+}
+
+int pt_batch_create_full(pt_ctx* c, const pt_block_spec* specs, const double* ext_bounds, int nblocks,
+                         int group_ctas, pt_batch** out) {
+  if (!c) return PT_EINVAL;
+  if (c->objective != PT_OBJ_CHI2 || c->strategy != PT_DE_RAND1_BIN)
+    return fail(c, PT_EINVAL, "the full model runs on the chi-square and DE/rand/1/bin only");
+  return create_batch(c, specs, ext_bounds, nblocks, PT_TIER_F64, group_ctas, HOST_MODEL_FULL, out);
+}
+
 int pt_batch_run(pt_batch* b) {
   if (!b) return PT_EINVAL;
   pt_ctx* c = b->ctx;
@@ -328,7 +359,7 @@ int pt_batch_run(pt_batch* b) {
     PT_CUDA(c, cudaGraphLaunch(b->exec, s));
   } else {
     const int rc = launch_de_groups(c, s, b->tier, b->blocks.data(), b->nblocks, b->sched.data(), b->off.data(),
-                                    b->ngroups, b->k, b->d_desc, b->d_ring, b->d_err, DE_LAUNCH);
+                                    b->ngroups, b->k, b->d_desc, b->d_ring, b->d_err, DE_LAUNCH, b->model);
     if (rc != PT_OK) return rc;
   }
   PT_CUDA(c, cudaEventRecord(b->ev1, s));
@@ -338,15 +369,29 @@ int pt_batch_run(pt_batch* b) {
   return PT_OK;
 }
 
-int pt_batch_results(pt_batch* b, pt_fit* out) {
+int pt_batch_results_full(pt_batch* b, double* out) {
   if (!b || !out) return PT_EINVAL;
   pt_ctx* c = b->ctx;
-  std::vector<double> h((size_t)b->nblocks * 6);
+  const int w = b->dim + 1;
+  std::vector<double> h((size_t)b->nblocks * w);
   PT_CUDA(c, cudaMemcpyAsync(h.data(), b->d_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PT_CUDA(c, cudaStreamSynchronize(c->stream));
   for (int i = 0; i < b->nblocks; ++i) {
-    for (int j = 0; j < 5; ++j) out[i].params[j] = h[(size_t)i * 6 + j];
-    out[i].sse = h[(size_t)i * 6 + 5];
+    double* o = out + (size_t)i * 8;
+    for (int j = 0; j < 7; ++j) o[j] = j < b->dim ? h[(size_t)i * w + j] : 0.0;
+    o[7] = h[(size_t)i * w + b->dim];
+  }
+  return PT_OK;
+}
+
+int pt_batch_results(pt_batch* b, pt_fit* out) {
+  if (!b || !out) return PT_EINVAL;
+  std::vector<double> h((size_t)b->nblocks * 8);
+  const int rc = pt_batch_results_full(b, h.data());
+  if (rc != PT_OK) return rc;
+  for (int i = 0; i < b->nblocks; ++i) {
+    for (int j = 0; j < 5; ++j) out[i].params[j] = h[(size_t)i * 8 + j];
+    out[i].sse = h[(size_t)i * 8 + 7];
   }
   return PT_OK;
 }

@@ -93,6 +93,7 @@ struct pt_ctx {
   double tune_rate = 0.0, tune_fixed_s = 0.0;
   double tune_rate_stream = 0.0;  // per-CTA rate when a CTA's tiles are staged chunk by chunk
   int tune_res_tiles = 0;         // tiles one CTA keeps resident (its shared-memory capacity)
+  int tune_model = 0;             // the model the cached rates were measured on
   bool tuned = false;
   pt_serve_state* serve = nullptr;
 };

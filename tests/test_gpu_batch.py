@@ -76,3 +76,33 @@ def test_batch_invalid(ctx):
     b.pop = 3
     with pytest.raises(pt.PhaseTrackError):
         pt.Batch(ctx, [b])
+
+
+def test_full_model_batch_bit_identical_to_single_solves(ctx):
+    # the full model's blocks (amplitude slope, order-4 phase) in one launch:
+    # every fit equals pt_de_solve_full on the block alone, and its SSE the
+    # oracle's evaluation of the returned parameters
+    import paper_1906_10598_b300 as pt
+    blocks = []
+    for i, (n, st, pop) in enumerate([(30_000, synth.I16, 32), (4_000, synth.F32, 48), (77_777, synth.I8, 64),
+                                      (257, synth.I16, 8)]):
+        b = synth.perigee400k(20 + i, n=n, storage=st, pop=pop, gens=30)
+        b.block_id, b.de_seed = 50 + i, 3 + i
+        blocks.append(b)
+    alone = []
+    for b in blocks:
+        ctx.load_block(b.samples, b.fs, b.t0, b.scale)
+        alone.append(ctx.de_solve_full(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, block_id=b.block_id))
+    for k in (0, 2):
+        batch = pt.Batch(ctx, blocks, group_ctas=k)
+        batch.run()
+        params, sse = batch.results()
+        assert params.shape == (len(blocks), 7)
+        for i, (p1, s1) in enumerate(alone):
+            assert np.array_equal(params[i], p1) and sse[i] == s1, (k, i)
+        batch.close()
+    for i, b in enumerate(blocks[:2]):
+        assert sse[i] == pytest.approx(oracle.sse_full(b.values(), b.fs, b.t0, params[i]), rel=1e-6)
+    # the cubic and full models do not mix in one batch
+    with pytest.raises(ValueError):
+        pt.Batch(ctx, [blocks[0], synth.paper400k(1, n=1000, gens=3)])
