@@ -145,13 +145,14 @@ PT_API void* pt_get_stream(const pt_ctx* ctx);
 PT_API int pt_load_block(pt_ctx* ctx, const void* samples, int64_t n, int dtype, double scale, double fs, double t0);
 
 /* Objective of the context's later pt_objective, pt_de_solve[_ex], pt_track
- * and pt_batch calls (and of a serving loop configured afterwards): PT_OBJ_CHI2
+ * and pt_batch calls, and of its serving loop, which takes the objective and
+ * the strategy in force when it starts (its first pt_submit): PT_OBJ_CHI2
  * (default) or PT_OBJ_COR. Values returned as "sse" are then the objective
  * value. Errors: PT_EINVAL. */
 PT_API int pt_set_objective(pt_ctx* ctx, int objective);
 
 /* DE strategy of the context's later pt_de_solve[_ex], pt_track and
- * pt_batch calls: PT_DE_RAND1_BIN (default), PT_DE_BEST1_JITTER or
+ * pt_batch calls, and of its serving loop when it starts: PT_DE_RAND1_BIN (default), PT_DE_BEST1_JITTER or
  * PT_DE_EITHER_OR. Errors: PT_EINVAL. */
 PT_API int pt_set_strategy(pt_ctx* ctx, int strategy);
 
@@ -306,10 +307,16 @@ PT_API void pt_batch_destroy(pt_batch* batch);
  * finished fit. A block's fit is bit-identical to pt_de_solve_ex on the same
  * block alone, whatever else is in flight. */
 
+/* Models of a served request. */
+#define PT_MODEL_CUBIC 0 /* (A, phi0, f0, f1, f2): block.bounds */
+#define PT_MODEL_FULL 1  /* the full model of pt_de_solve_full: block.bounds, then ext_bounds for A1, f3 */
+
 typedef struct pt_request {
   pt_block_spec block; /* samples are copied by pt_submit */
-  int tier;
+  int tier;            /* PT_TIER_* (the full model runs the default tier) */
   int stream_id;       /* caller's station-stream id, returned in the result */
+  int model;           /* PT_MODEL_CUBIC (0, the default of a zeroed request) or PT_MODEL_FULL */
+  double ext_bounds[4]; /* PT_MODEL_FULL: (lo, hi) for A1 and f3 */
 } pt_request;
 
 typedef struct pt_result {
@@ -319,6 +326,7 @@ typedef struct pt_result {
   double t_submit;     /* seconds on the library's monotonic clock (pt_clock) */
   double t_admit;      /* when the block started on the device */
   double t_done;       /* when the worker saw the fit complete */
+  double ext_params[2]; /* PT_MODEL_FULL: the fit's A1 and f3 (0 otherwise) */
 } pt_result;
 
 /* Configure the serving loop (before the first pt_submit; later calls fail

@@ -395,13 +395,14 @@ class Batch:
 
 class Request(ctypes.Structure):
     """Mirror of ``pt_request``."""
-    _fields_ = [("block", BlockSpec), ("tier", ctypes.c_int), ("stream_id", ctypes.c_int)]
+    _fields_ = [("block", BlockSpec), ("tier", ctypes.c_int), ("stream_id", ctypes.c_int), ("model", ctypes.c_int),
+                ("ext_bounds", ctypes.c_double * 4)]
 
 
 class Result(ctypes.Structure):
     """Mirror of ``pt_result``."""
     _fields_ = [("fit", Fit), ("status", ctypes.c_int), ("stream_id", ctypes.c_int), ("t_submit", ctypes.c_double),
-                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("ext_params", ctypes.c_double * 2)]
 
 
 def _serve_protos(lib):
@@ -501,6 +502,7 @@ class Server:
                  max_queued: int = 64):
         self._ctx = ctx
         self._lib = ctx._lib
+        self._models = {}  # ticket -> model of the request
         _serve_protos(self._lib)
         ctx._check(self._lib.pt_serve_configure(ctx.handle, int(max_inflight), int(ctas_per_request),
                                                 int(mem_budget_bytes), int(max_queued)))
@@ -514,8 +516,14 @@ class Server:
         sp.dtype = _NP_TO_PT[s.dtype]
         sp.scale, sp.fs, sp.t0 = float(block.scale), float(block.fs), float(block.t0)
         bb = np.asarray(block.bounds if bounds is None else bounds, dtype=np.float64).reshape(-1)
+        if bb.size not in (10, 14):
+            raise ValueError("submit: bounds must be 5 x 2 or 7 x 2")
         for j in range(10):
             sp.bounds[j] = float(bb[j])
+        if bb.size == 14:  # the full model
+            r.model = 1
+            for j in range(4):
+                r.ext_bounds[j] = float(bb[10 + j])
         sp.pop, sp.gens = int(block.pop), int(block.gens)
         sp.F, sp.CR = float(block.F), float(block.CR)
         sp.seed, sp.block_id = int(block.de_seed), int(block.block_id)
@@ -525,6 +533,7 @@ class Server:
         if rc == PT_EAGAIN:
             return None
         self._ctx._check(rc)
+        self._models[int(t.value)] = int(r.model)
         return int(t.value)
 
     def poll(self, ticket: int):
@@ -533,7 +542,10 @@ class Server:
         if rc == PT_PENDING:
             return None
         self._ctx._check(rc)
-        return {"params": np.array(list(r.fit.params)), "sse": r.fit.sse, "status": r.status,
+        params = list(r.fit.params)
+        if self._models.pop(ticket, 0) == 1:
+            params += list(r.ext_params)
+        return {"params": np.array(params), "sse": r.fit.sse, "status": r.status,
                 "stream_id": r.stream_id, "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done}
 
     def clock(self) -> float:

@@ -51,7 +51,8 @@ struct Slot {
   int* d_err = nullptr;
   double* d_out = nullptr;
   void* d_desc = nullptr;
-  double* h_out = nullptr;  // pinned: 6 doubles + the error word
+  double* h_out = nullptr;  // pinned: 8 doubles (the fit, dim + 1 used) + the error word
+  int dim = HOST_D;         // parameters of the running fit
   bool busy = false;
   uint64_t ticket = 0;
   int stream_id = 0;
@@ -84,9 +85,9 @@ int slot_init(pt_serve_state* S, Slot& sl) {
   PT_CUDA(w, cudaMalloc(&sl.d_u64, sizeof(unsigned long long)));
   PT_CUDA(w, cudaMalloc(&sl.d_ring, RING_GROUP_WORDS * sizeof(unsigned long long)));
   PT_CUDA(w, cudaMalloc(&sl.d_err, sizeof(int)));
-  PT_CUDA(w, cudaMalloc(&sl.d_out, 6 * sizeof(double)));
+  PT_CUDA(w, cudaMalloc(&sl.d_out, 8 * sizeof(double)));
   PT_CUDA(w, cudaMalloc(&sl.d_desc, de_desc_bytes(1, 1)));
-  PT_CUDA(w, cudaMallocHost(&sl.h_out, 8 * sizeof(double)));
+  PT_CUDA(w, cudaMallocHost(&sl.h_out, 10 * sizeof(double)));
   return PT_OK;
 }
 
@@ -122,9 +123,11 @@ int admit(pt_serve_state* S, Slot& sl, Pending& p) {
                         sl.d_u64, &h.blk);
   S->held += sl.cap - before;
   if (rc != PT_OK) return rc;
-  for (int j = 0; j < HOST_D; ++j) {
-    h.lo[j] = b.bounds[2 * j];
-    h.hi[j] = b.bounds[2 * j + 1];
+  const bool full = p.req.model == PT_MODEL_FULL;
+  const int dim = full ? HOST_DMAX : HOST_D;
+  for (int j = 0; j < dim; ++j) {
+    h.lo[j] = j < HOST_D ? b.bounds[2 * j] : p.req.ext_bounds[2 * (j - HOST_D)];
+    h.hi[j] = j < HOST_D ? b.bounds[2 * j + 1] : p.req.ext_bounds[2 * (j - HOST_D) + 1];
   }
   h.pop = b.pop;
   h.gens = b.gens;
@@ -135,11 +138,12 @@ int admit(pt_serve_state* S, Slot& sl, Pending& p) {
   h.out = sl.d_out;
   const int sched[1] = {0}, off[2] = {0, 1};
   const int k = (int)std::max<int64_t>(1, std::min<int64_t>(h.blk.ntiles, S->ctas));
-  rc = launch_de_groups(w, sl.stream, p.req.tier, &h, 1, sched, off, 1, k, sl.d_desc, sl.d_ring, sl.d_err,
-                        DE_UPLOAD | DE_LAUNCH);
+  rc = launch_de_groups(w, sl.stream, full ? PT_TIER_F64 : p.req.tier, &h, 1, sched, off, 1, k, sl.d_desc,
+                        sl.d_ring, sl.d_err, DE_UPLOAD | DE_LAUNCH, full ? HOST_MODEL_FULL : HOST_MODEL_CUBIC);
   if (rc != PT_OK) return rc;
-  PT_CUDA(w, cudaMemcpyAsync(sl.h_out, sl.d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, sl.stream));
-  PT_CUDA(w, cudaMemcpyAsync(sl.h_out + 6, sl.d_err, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
+  PT_CUDA(w, cudaMemcpyAsync(sl.h_out, sl.d_out, (dim + 1) * sizeof(double), cudaMemcpyDeviceToHost, sl.stream));
+  PT_CUDA(w, cudaMemcpyAsync(sl.h_out + 8, sl.d_err, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
+  sl.dim = dim;
   PT_CUDA(w, cudaEventRecord(sl.done, sl.stream));
   sl.busy = true;
   sl.ticket = p.ticket;
@@ -150,12 +154,17 @@ int admit(pt_serve_state* S, Slot& sl, Pending& p) {
 }
 
 void finish(pt_serve_state* S, uint64_t ticket, int stream_id, double t_submit, double t_admit, const double* out,
-            int status) {
+            int dim, int status) {
   pt_result r;
   std::memset(&r, 0, sizeof(r));
-  if (out)
+  if (out) {
     for (int j = 0; j < 5; ++j) r.fit.params[j] = out[j];
-  r.fit.sse = out ? out[5] : 0.0;
+    if (dim == HOST_DMAX) {
+      r.ext_params[0] = out[5];
+      r.ext_params[1] = out[6];
+    }
+  }
+  r.fit.sse = out ? out[dim] : 0.0;
   r.status = status;
   r.stream_id = stream_id;
   r.t_submit = t_submit;
@@ -181,11 +190,12 @@ void worker_loop(pt_serve_state* S) {
         status = PT_ECUDA;
       } else {
         int derr;
-        std::memcpy(&derr, sl.h_out + 6, sizeof(int));
+        std::memcpy(&derr, sl.h_out + 8, sizeof(int));
         if (derr == 1) status = PT_ETIMEOUT;
         else if (derr != 0) status = PT_ECUDA;
       }
-      finish(S, sl.ticket, sl.stream_id, sl.t_submit, sl.t_admit, status == PT_OK ? sl.h_out : nullptr, status);
+      finish(S, sl.ticket, sl.stream_id, sl.t_submit, sl.t_admit, status == PT_OK ? sl.h_out : nullptr, sl.dim,
+             status);
       sl.busy = false;
       progressed = true;
     }
@@ -214,7 +224,7 @@ void worker_loop(pt_serve_state* S) {
       Pending job = std::move(p);
       S->queue.pop_front();
       const int rc = admit(S, *free_slot, job);
-      if (rc != PT_OK) finish(S, job.ticket, job.req.stream_id, job.t_submit, now_s(), nullptr, rc);
+      if (rc != PT_OK) finish(S, job.ticket, job.req.stream_id, job.t_submit, now_s(), nullptr, HOST_D, rc);
       progressed = true;
     }
     if (!progressed) S->cv.wait_for(lk, std::chrono::microseconds(50));
@@ -233,6 +243,9 @@ int ensure_started(pt_ctx* c) {
   S->wctx.sms = c->sms;
   S->wctx.smem_optin = c->smem_optin;
   S->wctx.timeout_ns = c->timeout_ns;
+  // the objective and strategy in force when the loop starts
+  S->wctx.objective = c->objective;
+  S->wctx.strategy = c->strategy;
   if (S->ctas <= 0) S->ctas = std::max(1, c->sms / S->max_inflight);
   if (S->budget == 0) {
     size_t fr = 0, tot = 0;
@@ -294,8 +307,19 @@ int pt_submit(pt_ctx* c, const pt_request* req, uint64_t* ticket) {
   if (!c) return PT_EINVAL;
   if (!req || !ticket) return fail(c, PT_EINVAL, "pt_submit: invalid argument");
   const pt_block_spec& b = req->block;
-  int rc = check_de_args(c, b.bounds, b.pop, b.gens, b.F, b.CR, req->tier);
+  if (req->model != PT_MODEL_CUBIC && req->model != PT_MODEL_FULL)
+    return fail(c, PT_EINVAL, "pt_submit: unknown model");
+  const bool full = req->model == PT_MODEL_FULL;
+  double bnd[14];
+  std::memcpy(bnd, b.bounds, sizeof(double) * 10);
+  if (full) std::memcpy(bnd + 10, req->ext_bounds, sizeof(double) * 4);
+  int rc = check_de_args(c, bnd, b.pop, b.gens, b.F, b.CR, full ? PT_TIER_F64 : req->tier,
+                         full ? HOST_DMAX : HOST_D);
   if (rc != PT_OK) return rc;
+  const int obj = c->serve && c->serve->started ? c->serve->wctx.objective : c->objective;
+  const int strat = c->serve && c->serve->started ? c->serve->wctx.strategy : c->strategy;
+  if (full && (obj != PT_OBJ_CHI2 || strat != PT_DE_RAND1_BIN))
+    return fail(c, PT_EINVAL, "pt_submit: the full model runs on the chi-square and DE/rand/1/bin only");
   const int es = esize_of(b.dtype);
   if (!b.samples || b.n < 1 || es == 0 || !(b.scale > 0.0) || !(b.fs > 0.0) || !std::isfinite(b.t0) ||
       b.n > ((int64_t)1 << 36))

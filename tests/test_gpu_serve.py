@@ -87,3 +87,59 @@ def test_queue_backpressure_and_small_budget(ctx):
     assert refused > 0  # PT_EAGAIN once the queue is full
     res = _wait(server, tickets)
     assert len(res) == len(tickets) and all(r["status"] == pt.PT_OK for r in res.values())
+
+
+def test_served_full_model_requests_bit_identical_to_alone():
+    # cubic and full-model requests (7 x 2 bounds) mixed in one serving loop
+    import paper_1906_10598_b300 as pt
+    c = pt.Context(0)
+    try:
+        blocks = []
+        for k in range(3):
+            blocks.append(synth.perigee400k(30 + k, n=20_000 + 999 * k, gens=40))
+            blocks.append(synth.paper400k(40 + k, n=15_000 + 777 * k, gens=40))
+        for i, b in enumerate(blocks):
+            b.block_id, b.de_seed = 200 + i, 9 + i
+        alone = []
+        for b in blocks:
+            c.load_block(b.samples, b.fs, b.t0, b.scale)
+            if b.bounds.shape[0] == 7:
+                alone.append(c.de_solve_full(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, block_id=b.block_id))
+            else:
+                alone.append(c.de_solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, pt.TIER_F64,
+                                        block_id=b.block_id))
+        server = pt.Server(c, max_inflight=2, ctas_per_request=16, max_queued=16)
+        tickets = [server.submit(b, pt.TIER_F64, stream_id=i) for i, b in enumerate(blocks)]
+        assert all(t is not None for t in tickets)
+        res = _wait(server, tickets)
+        assert len(res) == len(tickets)
+        for t, (p1, s1), b in zip(tickets, alone, blocks):
+            r = res[t]
+            assert r["status"] == 0 and len(r["params"]) == b.bounds.shape[0]
+            assert np.array_equal(r["params"], p1) and r["sse"] == s1
+    finally:
+        c.close()
+
+
+def test_serving_loop_takes_the_context_objective():
+    # the loop starts with the context's objective (the correlation objective
+    # here): served fits equal the context's own solves on it, and full-model
+    # requests, which run on the chi-square only, are refused
+    import paper_1906_10598_b300 as pt
+    c = pt.Context(0)
+    try:
+        c.set_objective("cor")
+        blk = synth.paper400k(3, n=20_000, gens=30)
+        b = blk.bounds.copy()
+        b[0] = (blk.truth[0], blk.truth[0])
+        c.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+        p1, s1 = c.de_solve(b, blk.pop, blk.gens, blk.F, blk.CR, blk.de_seed, pt.TIER_F64, block_id=blk.block_id)
+        server = pt.Server(c, max_inflight=1, ctas_per_request=16)
+        t = server.submit(blk, pt.TIER_F64, bounds=b)
+        r = _wait(server, [t])[t]
+        assert r["status"] == 0 and np.array_equal(r["params"], p1) and r["sse"] == s1
+        with pytest.raises(pt.PhaseTrackError):
+            server.submit(synth.perigee400k(1, n=5_000, gens=5))
+    finally:
+        c.set_objective("chi2")
+        c.close()
