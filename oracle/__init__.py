@@ -114,9 +114,15 @@ def _load():
                                                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_uint64, ctypes.c_uint32, dp, dp, dp, ctypes.c_int]
         lib.oc_de_solve_block_full.restype = ctypes.c_int
-        lib.oc_de_textbook_dim.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
-                                           ctypes.c_double, ctypes.c_double, ctypes.c_uint64, dp]
-        lib.oc_de_textbook_dim.restype = ctypes.c_int
+        lib.oc_de_textbook_dim_strategy.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
+                                                    dp]
+        lib.oc_de_textbook_dim_strategy.restype = ctypes.c_int
+        lib.oc_de_solve_block_full_strategy.argtypes = [dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, dp,
+                                                        ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                        ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, dp, dp, dp,
+                                                        ctypes.c_int]
+        lib.oc_de_solve_block_full_strategy.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -261,19 +267,19 @@ def sse_full_many(samples, fs: float, t0: float, cands, nthreads: int = 0) -> np
 
 
 def de_solve_full(samples, fs: float, t0: float, bounds, pop: int, gens: int, F: float, CR: float, seed: int,
-                  block_id: int = 0, nthreads: int = 0, return_population: bool = False):
-    """DE/rand/1/bin fit of the full model (7 parameters) on the chi-square.
-    A parameter whose bounds are equal is held there (A1 = 0 or f3 = 0 gives
-    the 6-parameter forms)."""
+                  block_id: int = 0, nthreads: int = 0, return_population: bool = False, strategy: str = "rand1bin"):
+    """DE fit of the full model (7 parameters) on the chi-square (DE/rand/1/bin
+    by default, or the strategies "3" and "6"). A parameter whose bounds are
+    equal is held there (A1 = 0 or f3 = 0 gives the 6-parameter forms)."""
     s = _f64(samples)
     b = _f64(bounds).reshape(DF, 2)
     out = np.zeros(DF + 1, dtype=np.float64)
     popv = np.zeros((pop, DF), dtype=np.float64)
     fit = np.zeros(pop, dtype=np.float64)
-    rc = _load().oc_de_solve_block_full(_dptr(s), s.size, float(fs), float(t0), _dptr(b), int(pop), int(gens),
-                                        float(F), float(CR), ctypes.c_uint64(int(seed)),
-                                        ctypes.c_uint32(int(block_id)), _dptr(out), _dptr(popv), _dptr(fit),
-                                        int(nthreads))
+    rc = _load().oc_de_solve_block_full_strategy(_dptr(s), s.size, float(fs), float(t0), _dptr(b), int(pop),
+                                                 int(gens), float(F), float(CR), ctypes.c_uint64(int(seed)),
+                                                 ctypes.c_uint32(int(block_id)), int(STRATEGIES[strategy]),
+                                                 _dptr(out), _dptr(popv), _dptr(fit), int(nthreads))
     if rc != 0:
         raise ValueError("oracle de_solve_full: invalid arguments")
     if return_population:
@@ -281,13 +287,15 @@ def de_solve_full(samples, fs: float, t0: float, bounds, pop: int, gens: int, F:
     return out[:DF].copy(), float(out[DF])
 
 
-def de_textbook_dim(which: str, bounds, pop: int, gens: int, F: float, CR: float, seed: int):
-    """The oracle's DE (rand/1/bin) on a textbook function of len(bounds) parameters (5 or 7)."""
+def de_textbook_dim(which: str, bounds, pop: int, gens: int, F: float, CR: float, seed: int,
+                    strategy: str = "rand1bin"):
+    """The oracle's DE on a textbook function of len(bounds) parameters (5 or 7)."""
     b = _f64(bounds).reshape(-1, 2)
     dim = b.shape[0]
     out = np.zeros(dim + 1, dtype=np.float64)
-    rc = _load().oc_de_textbook_dim(0 if which == "sphere" else 1, dim, _dptr(b), int(pop), int(gens), float(F),
-                                    float(CR), ctypes.c_uint64(int(seed)), _dptr(out))
+    rc = _load().oc_de_textbook_dim_strategy(0 if which == "sphere" else 1, dim, _dptr(b), int(pop), int(gens),
+                                             float(F), float(CR), ctypes.c_uint64(int(seed)),
+                                             int(STRATEGIES[strategy]), _dptr(out))
     if rc != 0:
         raise ValueError("oracle de_textbook_dim: invalid arguments")
     return out[:dim].copy(), float(out[dim])

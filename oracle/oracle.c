@@ -307,17 +307,17 @@ int oc_de_run(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], in
                             final_fit, nthreads);
 }
 
-/* DE over `dim` parameters: 5 for the cubic model, 7 for the full model (the
- * strategies other than rand/1/bin are defined for 5). Generation 0 draws
- * component j from words 2j and 2j+1 of oc_draw16 (the same words as
- * oc_draw12's for dim 5); later generations draw as for dim 5, with the
- * crossover word of component j at word 4 + j. */
+/* DE over `dim` parameters: 5 for the cubic model, 7 for the full model.
+ * Generation 0 draws component j from words 2j and 2j+1 of oc_draw16 (the
+ * same words as oc_draw12's for dim 5); later generations draw as for dim 5,
+ * with the crossover word of component j at word 4 + j and, for DE/best/1
+ * with jitter, the jitter word of component j at word 9 + j (j < 3), else
+ * word j - 3 of the fourth counter group. */
 int oc_de_run_dim(oc_objective_fn obj, void* user, int dim, const double* bounds, int np, int gens, double F,
                   double CR, uint64_t seed, uint32_t block_id, int strategy, double* out, double* final_pop,
                   double* final_fit, int nthreads) {
   if (np < 4 || gens < 0 || (dim != OC_D && dim != OC_DF)) return -1;
   if (strategy != OC_DE_RAND1_BIN && strategy != OC_DE_BEST1_JITTER && strategy != OC_DE_EITHER_OR) return -1;
-  if (dim != OC_D && strategy != OC_DE_RAND1_BIN) return -1;
   double lo[OC_DF], hi[OC_DF];
   for (int j = 0; j < dim; ++j) {
     lo[j] = bounds[2 * j];
@@ -433,14 +433,24 @@ static double oc_block_full_objective(const double* th, void* user) {
   return oc_sse_full(b->s, b->n, b->fs, b->t0, th);
 }
 
+/* DE fit of the full model (7 parameters) on the chi-square with one of the
+ * strategies (Table 3-1-1 pairs "3" with the chi-square). */
+int oc_de_solve_block_full_strategy(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_DF],
+                                    int np, int gens, double F, double CR, uint64_t seed, uint32_t block_id,
+                                    int strategy, double out[OC_DF + 1], double* final_pop, double* final_fit,
+                                    int nthreads) {
+  if (n < 1 || !(fs > 0.0)) return -1;
+  oc_block b = {s, n, fs, t0};
+  return oc_de_run_dim(oc_block_full_objective, &b, OC_DF, bounds, np, gens, F, CR, seed, block_id, strategy, out,
+                       final_pop, final_fit, nthreads);
+}
+
 /* DE/rand/1/bin fit of the full model (7 parameters) on the chi-square. */
 int oc_de_solve_block_full(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_DF], int np,
                            int gens, double F, double CR, uint64_t seed, uint32_t block_id, double out[OC_DF + 1],
                            double* final_pop, double* final_fit, int nthreads) {
-  if (n < 1 || !(fs > 0.0)) return -1;
-  oc_block b = {s, n, fs, t0};
-  return oc_de_run_dim(oc_block_full_objective, &b, OC_DF, bounds, np, gens, F, CR, seed, block_id, OC_DE_RAND1_BIN,
-                       out, final_pop, final_fit, nthreads);
+  return oc_de_solve_block_full_strategy(s, n, fs, t0, bounds, np, gens, F, CR, seed, block_id, OC_DE_RAND1_BIN, out,
+                                         final_pop, final_fit, nthreads);
 }
 
 int oc_de_solve_block(const double* s, int64_t n, double fs, double t0, const double bounds[2 * OC_D], int np,
@@ -497,10 +507,15 @@ static double oc_rosenbrock_n(const double* x, void* user) {
   return s;
 }
 
+int oc_de_textbook_dim_strategy(int which, int dim, const double* bounds, int np, int gens, double F, double CR,
+                                uint64_t seed, int strategy, double* out) {
+  oc_objective_fn f = which == 0 ? oc_sphere_n : oc_rosenbrock_n;
+  return oc_de_run_dim(f, &dim, dim, bounds, np, gens, F, CR, seed, 0u, strategy, out, NULL, NULL, 1);
+}
+
 int oc_de_textbook_dim(int which, int dim, const double* bounds, int np, int gens, double F, double CR,
                        uint64_t seed, double* out) {
-  oc_objective_fn f = which == 0 ? oc_sphere_n : oc_rosenbrock_n;
-  return oc_de_run_dim(f, &dim, dim, bounds, np, gens, F, CR, seed, 0u, OC_DE_RAND1_BIN, out, NULL, NULL, 1);
+  return oc_de_textbook_dim_strategy(which, dim, bounds, np, gens, F, CR, seed, OC_DE_RAND1_BIN, out);
 }
 
 /* ------------------------------------------------------------------------ */

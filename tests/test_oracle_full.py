@@ -154,3 +154,23 @@ def test_de_full_fixed_parameter_by_equal_bounds():
     assert np.all(np.isfinite(fit))
     with pytest.raises(ValueError):
         oracle.de_solve_full(x, fs, t0, b[:5], 32, 10, 0.7, 0.9, 4)
+
+
+@pytest.mark.parametrize("strategy", ["best1jitter", "eitheror"])
+def test_de_dim7_strategies_known_minima(strategy):
+    # the paper's strategies "3" and "6" over 7 parameters: the sphere's and
+    # Rosenbrock's known minima, and the noise-free full-model block's truth
+    b = np.tile([-5.0, 5.0], (7, 1))
+    x, f = oracle.de_textbook_dim("sphere", b, 40, 600, 0.7, 0.9, 5, strategy=strategy)
+    assert f < 1e-12 and np.all(np.abs(x) < 1e-5)
+    b = np.tile([-2.0, 2.0], (7, 1))
+    x, f = oracle.de_textbook_dim("rosenbrock", b, 70, 2000, 0.7, 0.9, 6, strategy=strategy)
+    assert f < 1e-8 and np.all(np.abs(x - 1.0) < 1e-3)
+    x, fs, t0, truth, bounds = _clean_full_block()
+    p, f = oracle.de_solve_full(x, fs, t0, bounds, 48, 1500, 0.7, 0.9, 3, strategy=strategy)
+    assert f < 1e-10 * len(x) and np.allclose(p[[0, 2, 3, 4, 5]], truth[[0, 2, 3, 4, 5]], rtol=0, atol=1e-4)
+    # over 5 parameters the dimension-general DE is the 5-parameter one
+    b5 = np.tile([-2.0, 2.0], (5, 1))
+    a = oracle.de_textbook("rosenbrock", b5, 24, 150, 0.7, 0.9, 11, strategy=strategy)
+    c = oracle.de_textbook_dim("rosenbrock", b5, 24, 150, 0.7, 0.9, 11, strategy=strategy)
+    assert np.array_equal(a[0], c[0]) and a[1] == c[1]
