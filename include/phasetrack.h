@@ -194,10 +194,12 @@ PT_API int pt_de_solve_ex(pt_ctx* ctx, const double* bounds, int pop, int gens, 
  * theta = (A, phi0, f0, f1, f2, A1, f3):
  *   m(t) = (A + A1 t) cos(phi0 + 2 pi (f0 t + f1 t^2/2 + f2 t^3/6 + f3 t^4/24)),
  * i.e. c4 = A, c5 = A1 and the order-4 phase coefficient f3 (cycles/s^4). The
- * default tier (PT_TIER_F64 arithmetic) and the chi-square of Eq. 2-2-4 only:
- * both calls fail with PT_EINVAL unless the context's objective is
- * PT_OBJ_CHI2 and its strategy PT_DE_RAND1_BIN. A parameter held at lo = hi
- * stays there, so A1 = 0 or f3 = 0 gives the 6-parameter forms. */
+ * default tier (PT_TIER_F64 arithmetic) and the chi-square of Eq. 2-2-4 only
+ * (Eq. 2-2-5's model has a constant amplitude): the full-model calls fail
+ * with PT_EINVAL unless the context's objective is PT_OBJ_CHI2. Every DE
+ * strategy applies (the paper's own setting is Dim_XC = 6 with strategy
+ * "3"). A parameter held at lo = hi stays there, so A1 = 0 or f3 = 0 gives
+ * the 6-parameter forms. */
 
 /* Evaluate Eq. 2-2-4 of the full model for n candidates on the loaded block.
  *   cands    host or device pointer, n rows of 7 doubles, row-major.
@@ -206,10 +208,11 @@ PT_API int pt_de_solve_ex(pt_ctx* ctx, const double* bounds, int pop, int gens, 
  * Errors: PT_EINVAL, PT_ENOBLOCK, PT_ENOMEM, PT_ECUDA, PT_ETIMEOUT. */
 PT_API int pt_objective_full(pt_ctx* ctx, const double* cands, int64_t n, double* sse_out);
 
-/* Fit the loaded block with the full model by DE/rand/1/bin, as
+/* Fit the loaded block with the full model by the context's DE strategy, as
  * pt_de_solve_ex over 7 parameters. The draws are pt_de_solve_ex's, with the
- * generation-0 words 12 and 13 of component 6 from counter (3, i, 0, block_id)
- * and the crossover words of components 5, 6 at words 9, 10.
+ * generation-0 words 12 and 13 of component 6 from counter (3, i, 0, block_id),
+ * the crossover words of components 5, 6 at words 9, 10 and (PT_DE_BEST1_JITTER)
+ * their jitter words at words 2, 3 of counter (3, i, g, block_id).
  *   bounds      host pointer, 7 x 2 doubles.
  *   params_out  host or device pointer, 8 doubles: the best theta and its SSE.
  *   pop_out     optional host or device pointer, pop x 7 doubles.
@@ -274,7 +277,7 @@ PT_API int pt_batch_create(pt_ctx* ctx, const pt_block_spec* specs, int nblocks,
                            pt_batch** out);
 
 /* A batch of full-model fits (pt_de_solve_full: amplitude slope and order-4
- * phase, default tier, chi-square, DE/rand/1/bin; PT_EINVAL otherwise):
+ * phase, default tier, chi-square; PT_EINVAL otherwise):
  * specs[i].bounds holds block i's first five (lo, hi) pairs and
  * ext_bounds[4 i .. 4 i + 3] its A1 and f3 pairs (host pointer, nblocks x 4).
  * The autotuner calibrates on the full model (its cache records the model).
@@ -483,7 +486,7 @@ PT_API int pt_track_create(pt_ctx* ctx, const pt_track_config* cfg, const double
  * bounds holds 7 (lo, hi) pairs; later blocks take pt_warm_bounds_full with
  * the initial A1 range, acceptance uses pt_continuity_full, and a retry also
  * widens the f3 range. cfg->tier is not used (the full model runs the default
- * tier); the context must be on the chi-square and DE/rand/1/bin (the fits
+ * tier); the context must be on the chi-square (the fits
  * fail with PT_EINVAL otherwise). Errors: PT_EINVAL, PT_ENOMEM. */
 PT_API int pt_track_create_full(pt_ctx* ctx, const pt_track_config* cfg, const double bounds[14], pt_track** out);
 

@@ -539,11 +539,11 @@ int de_solve_impl(pt_ctx* c, const double* bounds, int pop, int gens, double F, 
   return PT_OK;
 }
 
-// The full model runs the default tier, the chi-square and DE/rand/1/bin only.
+// The full model runs the default tier and the chi-square only (Eq. 2-2-5's
+// model has a constant amplitude); every DE strategy applies.
 int check_full_settings(pt_ctx* c) {
   if (c->objective != PT_OBJ_CHI2)
     return fail(c, PT_EINVAL, "the full model runs on the chi-square objective only");
-  if (c->strategy != PT_DE_RAND1_BIN) return fail(c, PT_EINVAL, "the full model runs DE/rand/1/bin only");
   return PT_OK;
 }
 

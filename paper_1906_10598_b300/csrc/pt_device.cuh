@@ -181,8 +181,8 @@ __device__ __forceinline__ long long dkey(double a) {
 // r1, r2, r3 packed in bytes 0..2 (distinct, != i), crossover mask in `take`
 // (bit j set = component j comes from the mutant).
 // DE_EITHER_OR marks a three-point trial in bit 24 of rpack and takes every
-// component; DE_BEST1_JITTER also writes the five jitter words of the trial
-// (words 9..11, then words 0..1 of a fourth counter group) to jit[0..4].
+// component; DE_BEST1_JITTER also writes the DIM jitter words of the trial
+// (words 9..11, then words 0..DIM-4 of a fourth counter group) to jit[0..DIM-1].
 template <int STRAT, int DIM = D>
 __device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, uint32_t gen, uint32_t* rpack,
                                          uint32_t* take, uint32_t* jit) {
@@ -195,6 +195,10 @@ __device__ __forceinline__ void de_draws(const DeControls& dc, int np, int i, ui
     jit[2] = w[11];
     jit[3] = g3.x;
     jit[4] = g3.y;
+    if (DIM > 5) {
+      jit[5] = g3.z;
+      jit[6] = g3.w;
+    }
   }
   // three distinct indices != i, by index shifting over the sorted exclusions
   uint32_t excl[4];

@@ -668,7 +668,8 @@ __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, 
   s.off_acc = o;
   o += align_up((size_t)npad * sizeof(unsigned long long), 16);
   s.off_draw = o;
-  o += align_up((size_t)(pop ? 7 * npad : 0) * sizeof(uint32_t), 16);  // rpack, take, 5 jitter words
+  // rpack, take and model_dim jitter words per individual
+  o += align_up((size_t)(pop ? (2 + model_dim(model)) * npad : 0) * sizeof(uint32_t), 16);
   s.off_anc = o;
   o += (tier == TIER_F64) ? (size_t)(nthreads / 32) * IPB * cgv * anchor_words(model) * sizeof(uint4) : 0;
   s.off_samp = o;
@@ -786,7 +787,7 @@ struct DeSmem {
   int* kexp;
   unsigned char* cub;
   unsigned long long* acc;
-  uint32_t *drp, *drt, *drj;  // packed indices, crossover mask, 5 jitter words per individual
+  uint32_t *drp, *drt, *drj;  // packed indices, crossover mask, model_dim jitter words per individual
   uint4* anc;
   float* s32;
   double* s64;
@@ -813,7 +814,7 @@ __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& s
   for (int t = threadIdx.x; t < DIM * npad; t += blockDim.x) {
     const int j = t / npad, c = t - j * npad;
     if (c < np)
-      sm.u[c * DIM + j] = de_component<STRAT, DIM>(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c], best, sm.drj + c * D);
+      sm.u[c * DIM + j] = de_component<STRAT, DIM>(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c], best, sm.drj + c * DIM);
   }
 }
 
@@ -826,7 +827,7 @@ __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& s
 // replaces a barrier, a fence and a separate read. `gg` counts the group's
 // generations across blocks so the ring discipline continues from block to
 // block. Returns false if a bounded wait expired or another CTA failed.
-// MODEL_FULL: the full model's 7 parameters (default tier, chi-square, DE/rand/1/bin).
+// MODEL_FULL: the full model's 7 parameters (default tier, chi-square).
 template <int TIER, int CGV, int OBJ, int MODEL = MODEL_CUBIC>
 __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long long* ring, unsigned long long& gg,
                          const DeSmem& sm, const DeLaunch& a, int* s_abort) {
@@ -862,12 +863,10 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     // trials u of this generation (the initial population at gen 0)
     if (gen == 0) {
       if (tid < np) de_init<DIM>(d.dc, tid, sm.u + tid * DIM);
-    } else if constexpr (MODEL == MODEL_FULL) {
-      mutate_all<DE_RAND1_BIN, DIM>(d, sm, np, npad);
     } else {
-      if (d.dc.strategy == DE_BEST1_JITTER) mutate_all<DE_BEST1_JITTER>(d, sm, np, npad);
-      else if (d.dc.strategy == DE_EITHER_OR) mutate_all<DE_EITHER_OR>(d, sm, np, npad);
-      else mutate_all<DE_RAND1_BIN>(d, sm, np, npad);
+      if (d.dc.strategy == DE_BEST1_JITTER) mutate_all<DE_BEST1_JITTER, DIM>(d, sm, np, npad);
+      else if (d.dc.strategy == DE_EITHER_OR) mutate_all<DE_EITHER_OR, DIM>(d, sm, np, npad);
+      else mutate_all<DE_RAND1_BIN, DIM>(d, sm, np, npad);
     }
     if (tid < npad) sm.acc[tid] = 0ull;
     __syncthreads();
@@ -928,14 +927,12 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     } else if (gen < d.gens && tid >= NP_MAX && tid < NP_MAX + np) {
       // the next generation's draws do not depend on selection: overlap them with the wait
       const int c = tid - NP_MAX;
-      if constexpr (MODEL == MODEL_FULL)
-        de_draws<DE_RAND1_BIN, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
-      else if (d.dc.strategy == DE_BEST1_JITTER)
-        de_draws<DE_BEST1_JITTER>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
+      if (d.dc.strategy == DE_BEST1_JITTER)
+        de_draws<DE_BEST1_JITTER, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * DIM);
       else if (d.dc.strategy == DE_EITHER_OR)
-        de_draws<DE_EITHER_OR>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
+        de_draws<DE_EITHER_OR, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * DIM);
       else
-        de_draws<DE_RAND1_BIN>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * D);
+        de_draws<DE_RAND1_BIN, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * DIM);
     }
     __syncthreads();
     if (*s_abort) return false;

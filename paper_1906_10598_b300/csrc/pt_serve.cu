@@ -317,9 +317,7 @@ int pt_submit(pt_ctx* c, const pt_request* req, uint64_t* ticket) {
                          full ? HOST_DMAX : HOST_D);
   if (rc != PT_OK) return rc;
   const int obj = c->serve && c->serve->started ? c->serve->wctx.objective : c->objective;
-  const int strat = c->serve && c->serve->started ? c->serve->wctx.strategy : c->strategy;
-  if (full && (obj != PT_OBJ_CHI2 || strat != PT_DE_RAND1_BIN))
-    return fail(c, PT_EINVAL, "pt_submit: the full model runs on the chi-square and DE/rand/1/bin only");
+  if (full && obj != PT_OBJ_CHI2) return fail(c, PT_EINVAL, "pt_submit: the full model runs on the chi-square only");
   const int es = esize_of(b.dtype);
   if (!b.samples || b.n < 1 || es == 0 || !(b.scale > 0.0) || !(b.fs > 0.0) || !std::isfinite(b.t0) ||
       b.n > ((int64_t)1 << 36))

@@ -9,7 +9,9 @@ Eq. 2-2-2 with Eq. 2-2-1 at n = 4, Sec. 3.2) against the oracle.
   early generations, and its fit matches the oracle's (phi0 within 1e-3 rad,
   f0 within 1e-5 Hz) on a perigee-shaped block.
 * Parameters held by equal bounds stay put; the entry points refuse the
-  correlation objective and the other strategies.
+  correlation objective. The strategies "3" and "6" run over the 7
+  parameters with the oracle's draws (early generations bit-identical), and
+  the paper's own setting (Dim_XC = 6, strategy "3") matches the oracle's fit.
 """
 import math
 
@@ -163,9 +165,39 @@ def test_de_full_fixed_parameters_and_errors(ctx):
             ctx.de_solve_full(b, 16, 5, 0.7, 0.9, 1)
     finally:
         ctx.set_objective("chi2")
+
+
+@pytest.mark.parametrize("strategy", ["best1jitter", "eitheror"])
+def test_de_full_strategies_early_generations_bit_identical(ctx, strategy):
+    blk = synth.perigee400k(8, n=8192, storage=synth.F64)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    ctx.set_strategy(strategy)
     try:
-        ctx.set_strategy("best1jitter")
-        with pytest.raises(pt.PhaseTrackError):
-            ctx.de_solve_full(b, 16, 5, 0.7, 0.9, 1)
+        for gens, CR in ((1, 0.9), (6, 0.9), (6, 1.0)):
+            _, _, gpop, gfit = ctx.de_solve_full(blk.bounds, 32, gens, 0.7, CR, 31, block_id=2,
+                                                 return_population=True)
+            _, _, opop, ofit = oracle.de_solve_full(blk.values(), blk.fs, blk.t0, blk.bounds, 32, gens, 0.7, CR, 31,
+                                                    block_id=2, return_population=True, strategy=strategy)
+            same = np.all(gpop == opop, axis=1)
+            assert same.sum() >= 31, (gens, CR, np.where(~same))
+            assert np.all(_rel(gfit[same], ofit[same]) <= 1e-6)
     finally:
         ctx.set_strategy("rand1bin")
+
+
+def test_de_full_paper_setting_dim6_strategy3(ctx):
+    # Table 3-1-1: Dim_XC = 6 (the amplitude slope, phase to order 3: f3 held
+    # at 0) with strategy "3" on the chi-square
+    blk = synth.perigee400k(9, n=20_000)
+    b = blk.bounds.copy()
+    b[6] = (0.0, 0.0)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    ctx.set_strategy("best1jitter")
+    try:
+        g, gf = ctx.de_solve_full(b, 48, 500, 0.7, 0.9, 13)
+    finally:
+        ctx.set_strategy("rand1bin")
+    o, of = oracle.de_solve_full(blk.values(), blk.fs, blk.t0, b, 48, 500, 0.7, 0.9, 13, strategy="best1jitter")
+    assert g[6] == 0.0 and o[6] == 0.0
+    assert abs(math.remainder(g[1] - o[1], 2 * math.pi)) < 1e-3 and abs(g[2] - o[2]) < 1e-5
+    assert gf == pytest.approx(oracle.sse_full(blk.values(), blk.fs, blk.t0, g), rel=1e-6)
