@@ -201,3 +201,27 @@ def test_de_full_paper_setting_dim6_strategy3(ctx):
     assert g[6] == 0.0 and o[6] == 0.0
     assert abs(math.remainder(g[1] - o[1], 2 * math.pi)) < 1e-3 and abs(g[2] - o[2]) < 1e-5
     assert gf == pytest.approx(oracle.sse_full(blk.values(), blk.fs, blk.t0, g), rel=1e-6)
+
+
+@pytest.mark.parametrize("storage", [synth.I8, synth.F16, synth.F32, synth.F64])
+def test_objective_full_storages(ctx, storage):
+    blk = synth.perigee400k(10, n=30_001, storage=storage)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    cands = np.vstack([_cands_in(blk.bounds, 31, 6), blk.truth[None, :]])
+    g = ctx.objective_full(cands)
+    o = oracle.sse_full_many(blk.values(), blk.fs, blk.t0, cands)
+    assert np.all(_rel(g, o) <= 1e-6), float(np.max(_rel(g, o)))
+
+
+@pytest.mark.parametrize("pop", [4, 5, 128])
+def test_de_full_population_extremes(ctx, pop):
+    # the smallest populations (a single item group, three donors for each
+    # trial) and the largest (the kernels' limit)
+    blk = synth.perigee400k(11, n=6_000, storage=synth.F64)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    _, _, gpop, gfit = ctx.de_solve_full(blk.bounds, pop, 3, 0.7, 0.9, 2, return_population=True)
+    _, _, opop, ofit = oracle.de_solve_full(blk.values(), blk.fs, blk.t0, blk.bounds, pop, 3, 0.7, 0.9, 2,
+                                            return_population=True)
+    same = np.all(gpop == opop, axis=1)
+    assert same.sum() >= pop - 1 and gpop.shape == (pop, 7)
+    assert np.all(_rel(gfit[same], ofit[same]) <= 1e-6)
