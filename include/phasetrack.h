@@ -194,19 +194,20 @@ PT_API int pt_de_solve_ex(pt_ctx* ctx, const double* bounds, int pop, int gens, 
  * theta = (A, phi0, f0, f1, f2, A1, f3):
  *   m(t) = (A + A1 t) cos(phi0 + 2 pi (f0 t + f1 t^2/2 + f2 t^3/6 + f3 t^4/24)),
  * i.e. c4 = A, c5 = A1 and the order-4 phase coefficient f3 (cycles/s^4). The
- * default tier (PT_TIER_F64 arithmetic) and the chi-square of Eq. 2-2-4 only
- * (Eq. 2-2-5's model has a constant amplitude): the full-model calls fail
- * with PT_EINVAL unless the context's objective is PT_OBJ_CHI2. Every DE
- * strategy applies (the paper's own setting is Dim_XC = 6 with strategy
+ * chi-square of Eq. 2-2-4 only (Eq. 2-2-5's model has a constant amplitude):
+ * the full-model calls fail with PT_EINVAL unless the context's objective is
+ * PT_OBJ_CHI2. Every precision tier and DE strategy applies (the paper's own setting is Dim_XC = 6 with strategy
  * "3"). A parameter held at lo = hi stays there, so A1 = 0 or f3 = 0 gives
  * the 6-parameter forms. */
 
 /* Evaluate Eq. 2-2-4 of the full model for n candidates on the loaded block.
  *   cands    host or device pointer, n rows of 7 doubles, row-major.
  *   sse_out  host or device pointer, n doubles.
+ *   tier     PT_TIER_* (the default tier's phase re-expansion carries the
+ *            quartic term; the others evaluate the quartic Horner form).
  * Deterministic (independent of the launch shape).
  * Errors: PT_EINVAL, PT_ENOBLOCK, PT_ENOMEM, PT_ECUDA, PT_ETIMEOUT. */
-PT_API int pt_objective_full(pt_ctx* ctx, const double* cands, int64_t n, double* sse_out);
+PT_API int pt_objective_full(pt_ctx* ctx, const double* cands, int64_t n, double* sse_out, int tier);
 
 /* Fit the loaded block with the full model by the context's DE strategy, as
  * pt_de_solve_ex over 7 parameters. The draws are pt_de_solve_ex's, with the
@@ -217,9 +218,10 @@ PT_API int pt_objective_full(pt_ctx* ctx, const double* cands, int64_t n, double
  *   params_out  host or device pointer, 8 doubles: the best theta and its SSE.
  *   pop_out     optional host or device pointer, pop x 7 doubles.
  *   fit_out     optional host or device pointer, pop doubles.
+ *   tier        PT_TIER_*.
  * Errors: PT_EINVAL, PT_ENOBLOCK, PT_ENOMEM, PT_ECUDA, PT_ETIMEOUT. */
 PT_API int pt_de_solve_full(pt_ctx* ctx, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
-                            uint32_t block_id, double* params_out, double* pop_out, double* fit_out);
+                            uint32_t block_id, double* params_out, double* pop_out, double* fit_out, int tier);
 
 /* ---- Batched fits ---------------------------------------------------------
  * Many independent blocks of uneven length, each with its own DE controls and
@@ -277,13 +279,13 @@ PT_API int pt_batch_create(pt_ctx* ctx, const pt_block_spec* specs, int nblocks,
                            pt_batch** out);
 
 /* A batch of full-model fits (pt_de_solve_full: amplitude slope and order-4
- * phase, default tier, chi-square; PT_EINVAL otherwise):
+ * phase, chi-square; PT_EINVAL otherwise) in the given tier:
  * specs[i].bounds holds block i's first five (lo, hi) pairs and
  * ext_bounds[4 i .. 4 i + 3] its A1 and f3 pairs (host pointer, nblocks x 4).
  * The autotuner calibrates on the full model (its cache records the model).
  * Results: pt_batch_results_full (pt_batch_results gives the first five). */
 PT_API int pt_batch_create_full(pt_ctx* ctx, const pt_block_spec* specs, const double* ext_bounds, int nblocks,
-                                int group_ctas, pt_batch** out);
+                                int tier, int group_ctas, pt_batch** out);
 
 /* Solve every block of the batch (synchronous). Errors: PT_ECUDA, PT_ETIMEOUT. */
 PT_API int pt_batch_run(pt_batch* batch);
@@ -316,7 +318,7 @@ PT_API void pt_batch_destroy(pt_batch* batch);
 
 typedef struct pt_request {
   pt_block_spec block; /* samples are copied by pt_submit */
-  int tier;            /* PT_TIER_* (the full model runs the default tier) */
+  int tier;            /* PT_TIER_* */
   int stream_id;       /* caller's station-stream id, returned in the result */
   int model;           /* PT_MODEL_CUBIC (0, the default of a zeroed request) or PT_MODEL_FULL */
   double ext_bounds[4]; /* PT_MODEL_FULL: (lo, hi) for A1 and f3 */
@@ -485,8 +487,7 @@ PT_API int pt_track_create(pt_ctx* ctx, const pt_track_config* cfg, const double
  * amplitude slope and order-4 phase, for arcs near perigee, Sec. 3.2):
  * bounds holds 7 (lo, hi) pairs; later blocks take pt_warm_bounds_full with
  * the initial A1 range, acceptance uses pt_continuity_full, and a retry also
- * widens the f3 range. cfg->tier is not used (the full model runs the default
- * tier); the context must be on the chi-square (the fits
+ * widens the f3 range. The context must be on the chi-square (the fits
  * fail with PT_EINVAL otherwise). Errors: PT_EINVAL, PT_ENOMEM. */
 PT_API int pt_track_create_full(pt_ctx* ctx, const pt_track_config* cfg, const double bounds[14], pt_track** out);
 

@@ -84,10 +84,10 @@ def load_library():
     lib.pt_de_solve_ex.argtypes = [vp, dp, c_int, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                    ctypes.c_uint32, vp, vp, vp, c_int]
     lib.pt_de_solve_ex.restype = c_int
-    lib.pt_objective_full.argtypes = [vp, vp, i64, vp]
+    lib.pt_objective_full.argtypes = [vp, vp, i64, vp, c_int]
     lib.pt_objective_full.restype = c_int
     lib.pt_de_solve_full.argtypes = [vp, dp, c_int, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
-                                     ctypes.c_uint32, vp, vp, vp]
+                                     ctypes.c_uint32, vp, vp, vp, c_int]
     lib.pt_de_solve_full.restype = c_int
     lib.pt_last_kernel_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.pt_last_kernel_ms.restype = c_int
@@ -204,10 +204,11 @@ class Context:
                                            int(tier)))
         return out
 
-    def objective_full(self, cands, out=None):
+    def objective_full(self, cands, tier: int = TIER_F64, out=None):
         """pt_objective_full: SSE of each full-model row (A, phi0, f0, f1, f2, A1, f3)."""
         c, n, out = self._cands_out(cands, 7, out)
-        self._check(self._lib.pt_objective_full(self._h, ctypes.c_void_p(_ptr(c)), n, ctypes.c_void_p(_ptr(out))))
+        self._check(self._lib.pt_objective_full(self._h, ctypes.c_void_p(_ptr(c)), n, ctypes.c_void_p(_ptr(out)),
+                                                int(tier)))
         return out
 
     def de_solve(self, bounds, pop: int, gens: int, F: float, CR: float, seed: int, tier: int = TIER_F64,
@@ -227,7 +228,7 @@ class Context:
         return out[:5].copy(), float(out[5])
 
     def de_solve_full(self, bounds, pop: int, gens: int, F: float, CR: float, seed: int, block_id: int = 0,
-                      return_population: bool = False):
+                      return_population: bool = False, tier: int = TIER_F64):
         """pt_de_solve_full: the full model's fit; returns (params[7], sse) or
         (params, sse, population[pop, 7], fitness)."""
         b = np.ascontiguousarray(np.asarray(bounds, dtype=np.float64).reshape(7, 2))
@@ -238,7 +239,7 @@ class Context:
             self._h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(pop), int(gens), float(F), float(CR),
             ctypes.c_uint64(int(seed)), ctypes.c_uint32(int(block_id)), ctypes.c_void_p(out.ctypes.data),
             ctypes.c_void_p(popv.ctypes.data if popv is not None else 0),
-            ctypes.c_void_p(fit.ctypes.data if fit is not None else 0)))
+            ctypes.c_void_p(fit.ctypes.data if fit is not None else 0), int(tier)))
         if return_population:
             return out[:7].copy(), float(out[7]), popv, fit
         return out[:7].copy(), float(out[7])
@@ -304,7 +305,7 @@ def _batch_protos(lib):
     lib.pt_batch_results.argtypes = [vp, ctypes.POINTER(Fit)]
     lib.pt_batch_results.restype = ctypes.c_int
     lib.pt_batch_create_full.argtypes = [vp, ctypes.POINTER(BlockSpec), ctypes.POINTER(ctypes.c_double),
-                                         ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
     lib.pt_batch_create_full.restype = ctypes.c_int
     lib.pt_batch_results_full.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.pt_batch_results_full.restype = ctypes.c_int
@@ -356,7 +357,7 @@ class Batch:
         if self._dim == 7:
             ctx._check(self._lib.pt_batch_create_full(ctx.handle, specs,
                                                       ext.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n,
-                                                      int(group_ctas), ctypes.byref(self._h)))
+                                                      int(tier), int(group_ctas), ctypes.byref(self._h)))
         else:
             ctx._check(self._lib.pt_batch_create(ctx.handle, specs, n, int(tier), int(group_ctas),
                                                  ctypes.byref(self._h)))

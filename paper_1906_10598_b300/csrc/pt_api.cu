@@ -118,10 +118,17 @@ int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
 
 int launch_objective_any(pt_ctx* c, int tier, const double* d_cands, int ncand, int model) {
   if (model == MODEL_FULL) {
-    const int cg = pick_cg(PT_TIER_F64, std::min(ncand, NP_MAX));
-    if (cg == 16) return launch_objective<TIER_F64, 16, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
-    if (cg == 8) return launch_objective<TIER_F64, 8, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
-    return launch_objective<TIER_F64, 4, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+    switch (tier) {
+      case PT_TIER_F64: {
+        const int cg = pick_cg(PT_TIER_F64, std::min(ncand, NP_MAX));
+        if (cg == 16) return launch_objective<TIER_F64, 16, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+        if (cg == 8) return launch_objective<TIER_F64, 8, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+        return launch_objective<TIER_F64, 4, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+      }
+      case PT_TIER_PLAIN: return launch_objective<TIER_PLAIN, 8, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+      case PT_TIER_DF32: return launch_objective<TIER_DF32, 8, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+      default: return launch_objective<TIER_F32, 8, OBJ_CHI2, MODEL_FULL>(c, d_cands, ncand);
+    }
   }
   if (c->objective == PT_OBJ_COR) {
     switch (tier) {
@@ -303,9 +310,14 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   PT_CUDA(c, cudaMemsetAsync(ring, 0, (size_t)ngroups * RING_GROUP_WORDS * sizeof(unsigned long long), s));
   PT_CUDA(c, cudaMemsetAsync(d_err, 0, sizeof(int), s));
   if (model == MODEL_FULL) {
-    // the full model: default tier, chi-square, DE/rand/1/bin (checked by the entry point)
+    // the full model: the chi-square (checked by the entry points)
     a.obj = OBJ_CHI2;
-    return launch_de_t<TIER_F64, OBJ_CHI2, MODEL_FULL>(c, s, a);
+    switch (tier) {
+      case PT_TIER_F64: return launch_de_t<TIER_F64, OBJ_CHI2, MODEL_FULL>(c, s, a);
+      case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN, OBJ_CHI2, MODEL_FULL>(c, s, a);
+      case PT_TIER_DF32: return launch_de_t<TIER_DF32, OBJ_CHI2, MODEL_FULL>(c, s, a);
+      default: return launch_de_t<TIER_F32, OBJ_CHI2, MODEL_FULL>(c, s, a);
+    }
   }
   a.obj = c->objective;
   if (a.obj == OBJ_COR) {
@@ -539,8 +551,8 @@ int de_solve_impl(pt_ctx* c, const double* bounds, int pop, int gens, double F, 
   return PT_OK;
 }
 
-// The full model runs the default tier and the chi-square only (Eq. 2-2-5's
-// model has a constant amplitude); every DE strategy applies.
+// The full model runs on the chi-square only (Eq. 2-2-5's model has a
+// constant amplitude); every tier and DE strategy applies.
 int check_full_settings(pt_ctx* c) {
   if (c->objective != PT_OBJ_CHI2)
     return fail(c, PT_EINVAL, "the full model runs on the chi-square objective only");
@@ -556,11 +568,11 @@ int pt_objective(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int
   return objective_impl(c, cands, n, sse_out, tier, MODEL_CUBIC);
 }
 
-int pt_objective_full(pt_ctx* c, const double* cands, int64_t n, double* sse_out) {
+int pt_objective_full(pt_ctx* c, const double* cands, int64_t n, double* sse_out, int tier) {
   if (!c) return PT_EINVAL;
   const int rc = check_full_settings(c);
   if (rc != PT_OK) return rc;
-  return objective_impl(c, cands, n, sse_out, PT_TIER_F64, MODEL_FULL);
+  return objective_impl(c, cands, n, sse_out, tier, MODEL_FULL);
 }
 
 int pt_de_solve_ex(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
@@ -570,12 +582,11 @@ int pt_de_solve_ex(pt_ctx* c, const double* bounds, int pop, int gens, double F,
 }
 
 int pt_de_solve_full(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,
-                     uint32_t block_id, double* params_out, double* pop_out, double* fit_out) {
+                     uint32_t block_id, double* params_out, double* pop_out, double* fit_out, int tier) {
   if (!c) return PT_EINVAL;
   const int rc = check_full_settings(c);
   if (rc != PT_OK) return rc;
-  return de_solve_impl(c, bounds, pop, gens, F, CR, seed, block_id, params_out, pop_out, fit_out, PT_TIER_F64,
-                       MODEL_FULL);
+  return de_solve_impl(c, bounds, pop, gens, F, CR, seed, block_id, params_out, pop_out, fit_out, tier, MODEL_FULL);
 }
 
 int pt_de_solve(pt_ctx* c, const double* bounds, int pop, int gens, double F, double CR, uint64_t seed,

@@ -341,11 +341,11 @@ int pt_batch_create(pt_ctx* c, const pt_block_spec* specs, int nblocks, int tier
   return create_batch(c, specs, nullptr, nblocks, tier, group_ctas, HOST_MODEL_CUBIC, out);
 }
 
-int pt_batch_create_full(pt_ctx* c, const pt_block_spec* specs, const double* ext_bounds, int nblocks,
+int pt_batch_create_full(pt_ctx* c, const pt_block_spec* specs, const double* ext_bounds, int nblocks, int tier,
                          int group_ctas, pt_batch** out) {
   if (!c) return PT_EINVAL;
   if (c->objective != PT_OBJ_CHI2) return fail(c, PT_EINVAL, "the full model runs on the chi-square only");
-  return create_batch(c, specs, ext_bounds, nblocks, PT_TIER_F64, group_ctas, HOST_MODEL_FULL, out);
+  return create_batch(c, specs, ext_bounds, nblocks, tier, group_ctas, HOST_MODEL_FULL, out);
 }
 
 int pt_batch_run(pt_batch* b) {

@@ -66,9 +66,36 @@ __device__ __forceinline__ dfloat df_from_double(double v) {
 //   TIER_PLAIN: double[5] = A, phi0/(2 pi), f0, f1/2, f2/6
 //   TIER_DF32:  dfloat[4] = c0..c3 (cycles, seconds), A in negA
 //   TIER_F32:   float[4]  = c0..c3
-template <int TIER, int OBJ = OBJ_CHI2>
+// MODEL_FULL (comparison tiers): the phase coefficients gain f3/24 and the
+// amplitude terms follow them; the exponent is the full model's.
+//   TIER_PLAIN: double[7] = A, A1, phi0/(2 pi), f0, f1/2, f2/6, f3/24
+//   TIER_DF32:  dfloat[5] = phi0/(2 pi), f0, f1/2, f2/6, f3/24, then float A, A1
+//   TIER_F32:   float[5] = the same, then float A, A1
+template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 __device__ __forceinline__ void prep_candidate(const double* th, const BlockArgs& b, unsigned char* cdata,
                                                float* negA, int* kexp, int kbits) {
+  if constexpr (MODEL == MODEL_FULL) {
+    *negA = 0.f;
+    *kexp = full_scale_exp(full_amp(th, b.t0, b.h), b.n, b.smax_f, kbits);
+    const double pc[5] = {th[1] * INV_TWO_PI, th[2], th[3] * 0.5, th[4] * (1.0 / 6.0), th[6] * (1.0 / 24.0)};
+    if (TIER == TIER_PLAIN) {
+      double* c = reinterpret_cast<double*>(cdata);
+      c[0] = th[0];
+      c[1] = th[5];
+      for (int k = 0; k < 5; ++k) c[2 + k] = pc[k];
+    } else if (TIER == TIER_DF32) {
+      dfloat* c = reinterpret_cast<dfloat*>(cdata);
+      for (int k = 0; k < 5; ++k) c[k] = df_from_double(pc[k]);
+      reinterpret_cast<float*>(cdata + 40)[0] = __double2float_rn(th[0]);
+      reinterpret_cast<float*>(cdata + 40)[1] = __double2float_rn(th[5]);
+    } else {
+      float* c = reinterpret_cast<float*>(cdata);
+      for (int k = 0; k < 5; ++k) c[k] = __double2float_rn(pc[k]);
+      c[5] = __double2float_rn(th[0]);
+      c[6] = __double2float_rn(th[5]);
+    }
+    return;
+  }
   const float Af = __double2float_rn(th[0]);
   *negA = -Af;
   *kexp = OBJ == OBJ_COR ? cor_scale_exp(b.n, b.smax_f, kbits) : sse_scale_exp(b.n, b.smax_f, fabsf(Af), kbits);
@@ -98,12 +125,13 @@ __device__ __forceinline__ void prep_candidate(const double* th, const BlockArgs
   }
 }
 
+template <int MODEL = MODEL_CUBIC>
 __device__ __forceinline__ void prep_zero(unsigned char* cdata, float* negA, int* kexp) {
   *negA = 0.f;
   *kexp = 0;
   uint4* p = reinterpret_cast<uint4*>(cdata);
 #pragma unroll
-  for (int k = 0; k < CAND_BYTES / 16; ++k) p[k] = make_uint4(0, 0, 0, 0);
+  for (int k = 0; k < cand_bytes(MODEL) / 16; ++k) p[k] = make_uint4(0, 0, 0, 0);
 }
 
 // Prepare candidates [0, nc) of `cands` (rows of 5 doubles) padded to npad.
@@ -116,7 +144,7 @@ __device__ __forceinline__ void prep_zero(unsigned char* cdata, float* negA, int
 template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs& b, unsigned char* cdata,
                          float* negA, int* kexp, unsigned char* cub, int kbits) {
-  if constexpr (MODEL == MODEL_FULL) {
+  if constexpr (MODEL == MODEL_FULL && TIER == TIER_F64) {
     for (int t = threadIdx.x; t < 6 * npad; t += blockDim.x) {
       const int k = t / npad, c = t - k * npad;
       const double* th = cands + c * DF;
@@ -142,7 +170,7 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
         kexp[c] = 0;
       }
     }
-  } else if (TIER == TIER_F64) {
+  } else if constexpr (TIER == TIER_F64) {
     for (int t = threadIdx.x; t < 5 * npad; t += blockDim.x) {
       const int k = t / npad, c = t - k * npad;
       if (k < 4) {
@@ -159,9 +187,12 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
       }
     }
   } else {
+    constexpr int CB = cand_bytes(MODEL);
     for (int c = threadIdx.x; c < npad; c += blockDim.x) {
-      if (c < nc) prep_candidate<TIER, OBJ>(cands + c * D, b, cdata + c * CAND_BYTES, negA + c, kexp + c, kbits);
-      else prep_zero(cdata + c * CAND_BYTES, negA + c, kexp + c);
+      if (c < nc)
+        prep_candidate<TIER, OBJ, MODEL>(cands + c * model_dim(MODEL), b, cdata + c * CB, negA + c, kexp + c, kbits);
+      else prep_zero<MODEL>(cdata + c * CB, negA + c, kexp + c);
+      cub[c] = 0;
     }
   }
   __syncthreads();
@@ -350,25 +381,33 @@ __device__ __forceinline__ void item_full_mixed(const float (&s)[M], const uint4
 
 // All-FP64 tier: Horner phase in seconds, reduction mod 1, FP64 cospi.
 // OBJ_COR accumulates s_i cos(phi_i) (the padding samples are zero).
-template <int CGV, bool MASKED, int OBJ = OBJ_CHI2>
+// MODEL_FULL: the quartic phase and the amplitude A + A1 t.
+template <int CGV, bool MASKED, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 __device__ __forceinline__ void item_plain(const double (&s)[M], const unsigned char* cdata_g, int lane, int nvalid,
                                            int64_t tstart, const BlockArgs& b, double (&acc)[CGV]) {
 #pragma unroll 1
   for (int c = 0; c < CGV; ++c) {
-    const double* k = reinterpret_cast<const double*>(cdata_g + c * CAND_BYTES);
-    const double A = k[0], c0 = k[1], c1 = k[2], c2 = k[3], c3 = k[4];
+    const double* k = reinterpret_cast<const double*>(cdata_g + c * cand_bytes(MODEL));
+    double A, A1 = 0.0, c0, c1, c2, c3, c4 = 0.0;
+    if constexpr (MODEL == MODEL_FULL) {
+      A = k[0], A1 = k[1], c0 = k[2], c1 = k[3], c2 = k[4], c3 = k[5], c4 = k[6];
+    } else {
+      A = k[0], c0 = k[1], c1 = k[2], c2 = k[3], c3 = k[4];
+    }
     double sum = 0.0;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       const int64_t i = tstart + lane * M + m;
       const double t = fma((double)i, b.h, b.t0);
-      const double p = fma(fma(fma(c3, t, c2), t, c1), t, c0);
+      const double p = MODEL == MODEL_FULL ? fma(fma(fma(fma(c4, t, c3), t, c2), t, c1), t, c0)
+                                           : fma(fma(fma(c3, t, c2), t, c1), t, c0);
       const double r = p - rint(p);
       const double cv = cospi(2.0 * r);
       if (OBJ == OBJ_COR) {
         sum = fma(s[m], cv, sum);
       } else {
-        double res = fma(-A, cv, s[m]);
+        const double Am = MODEL == MODEL_FULL ? fma(A1, t, A) : A;
+        double res = fma(-Am, cv, s[m]);
         if (MASKED) res = (lane * M + m < nvalid) ? res : 0.0;
         sum = fma(res, res, sum);
       }
@@ -378,27 +417,33 @@ __device__ __forceinline__ void item_plain(const double (&s)[M], const unsigned 
 }
 
 // Double-float tier: per-sample phase in double-float, FP32 cosine.
-template <int CGV, bool MASKED, int OBJ = OBJ_CHI2>
+template <int CGV, bool MASKED, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 __device__ __forceinline__ void item_df32(const float (&s)[M], const unsigned char* cdata_g, const float* negA_g,
                                           int lane, int nvalid, int64_t tstart, dfloat t0d, dfloat hd,
                                           float (&acc)[CGV]) {
 #pragma unroll 1
   for (int c = 0; c < CGV; ++c) {
-    const dfloat* k = reinterpret_cast<const dfloat*>(cdata_g + c * CAND_BYTES);
+    const dfloat* k = reinterpret_cast<const dfloat*>(cdata_g + c * cand_bytes(MODEL));
     const dfloat c0 = k[0], c1 = k[1], c2 = k[2], c3 = k[3];
-    const float nA = negA_g[c];
+    const dfloat c4 = MODEL == MODEL_FULL ? k[4] : dfloat{0.f, 0.f};
+    float nA = negA_g[c], A = 0.f, A1 = 0.f;
+    if constexpr (MODEL == MODEL_FULL) {
+      A = reinterpret_cast<const float*>(cdata_g + c * cand_bytes(MODEL) + 40)[0];
+      A1 = reinterpret_cast<const float*>(cdata_g + c * cand_bytes(MODEL) + 40)[1];
+    }
     float sum = 0.f;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       const int64_t i = tstart + lane * M + m;
       // t = t0 + i h in double-float (i < 2^24 is exact in FP32)
       const dfloat t = df_add(t0d, df_mul({(float)i, 0.f}, hd));
-      dfloat p = df_add(df_mul(c3, t), c2);
+      dfloat p = MODEL == MODEL_FULL ? df_add(df_mul(df_add(df_mul(c4, t), c3), t), c2) : df_add(df_mul(c3, t), c2);
       p = df_add(df_mul(p, t), c1);
       p = df_add(df_mul(p, t), c0);
       const float rh = p.hi - rintf(p.hi);
       const float r = rh + p.lo;
       const float cv = __cosf(r * 6.28318530717958648f);
+      if (MODEL == MODEL_FULL) nA = -fmaf(A1, t.hi, A);
       if (OBJ == OBJ_COR) {
         sum = fmaf(s[m], cv, sum);
       } else {
@@ -412,23 +457,27 @@ __device__ __forceinline__ void item_df32(const float (&s)[M], const unsigned ch
 }
 
 // Naive FP32 tier: Horner phase in seconds in FP32.
-template <int CGV, bool MASKED, int OBJ = OBJ_CHI2>
+template <int CGV, bool MASKED, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
 __device__ __forceinline__ void item_f32(const float (&s)[M], const unsigned char* cdata_g, const float* negA_g,
                                          int lane, int nvalid, int64_t tstart, float t0f, float hf,
                                          float (&acc)[CGV]) {
 #pragma unroll 1
   for (int c = 0; c < CGV; ++c) {
-    const float* k = reinterpret_cast<const float*>(cdata_g + c * CAND_BYTES);
+    const float* k = reinterpret_cast<const float*>(cdata_g + c * cand_bytes(MODEL));
     const float c0 = k[0], c1 = k[1], c2 = k[2], c3 = k[3];
-    const float nA = negA_g[c];
+    const float c4 = MODEL == MODEL_FULL ? k[4] : 0.f;
+    const float A = MODEL == MODEL_FULL ? k[5] : 0.f, A1 = MODEL == MODEL_FULL ? k[6] : 0.f;
+    float nA = negA_g[c];
     float sum = 0.f;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       const int64_t i = tstart + lane * M + m;
       const float t = fmaf((float)i, hf, t0f);
-      const float p = fmaf(fmaf(fmaf(c3, t, c2), t, c1), t, c0);
+      const float p = MODEL == MODEL_FULL ? fmaf(fmaf(fmaf(fmaf(c4, t, c3), t, c2), t, c1), t, c0)
+                                          : fmaf(fmaf(fmaf(c3, t, c2), t, c1), t, c0);
       const float r = p - rintf(p);
       const float cv = __cosf(r * 6.28318530717958648f);
+      if (MODEL == MODEL_FULL) nA = -fmaf(A1, t, A);
       if (OBJ == OBJ_COR) {
         sum = fmaf(s[m], cv, sum);
       } else {
@@ -502,7 +551,7 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
   constexpr int LPC = 32 / CGV;  // lanes holding each candidate's warp sum
 
   for (int base = item_lo + warp; base < nitems; base += nw * IPB) {
-    if constexpr (MODEL == MODEL_FULL) {
+    if constexpr (MODEL == MODEL_FULL && TIER == TIER_F64) {
       for (int q = lane; q < IPB * CGV; q += 32) {
         const int k = q / CGV, c = q - k * CGV;
         const int it = base + k * nw;
@@ -562,8 +611,9 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
           s[m + 1] = v.y;
         }
         double accv[CGV];
-        if (nvalid == L) item_plain<CGV, false, OBJ>(s, cdata + g * CGV * CAND_BYTES, lane, nvalid, tstart, b, accv);
-        else item_plain<CGV, true, OBJ>(s, cdata + g * CGV * CAND_BYTES, lane, nvalid, tstart, b, accv);
+        const unsigned char* cdp = cdata + g * CGV * cand_bytes(MODEL);
+        if (nvalid == L) item_plain<CGV, false, OBJ, MODEL>(s, cdp, lane, nvalid, tstart, b, accv);
+        else item_plain<CGV, true, OBJ, MODEL>(s, cdp, lane, nvalid, tstart, b, accv);
         const double z = warp_reduce_scatter<CGV>(accv, lane);
         if (owner) {
           const long long v = __double2ll_rn(z * __longlong_as_double((long long)(1023 + kexp[cand]) << 52));
@@ -581,8 +631,8 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
         }
         float accv[CGV];
         const float* nA = negA + g * CGV;
-        const unsigned char* cd = cdata + g * CGV * CAND_BYTES;
-        if constexpr (MODEL == MODEL_FULL) {
+        const unsigned char* cd = cdata + g * CGV * cand_bytes(MODEL);
+        if constexpr (MODEL == MODEL_FULL && TIER == TIER_F64) {
           const uint4* anc_i = anc_w + k * CGV * 2;
           if (nvalid == L) {
             if (any_flag<CGV>(cub + g * CGV)) item_full_mixed<CGV>(s, anc_i, cub + g * CGV, lane, accv);
@@ -599,11 +649,11 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
             item_f64<CGV, true, OBJ>(s, anc_i, nA, lane, nvalid, accv);
           }
         } else if (TIER == TIER_DF32) {
-          if (nvalid == L) item_df32<CGV, false, OBJ>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
-          else item_df32<CGV, true, OBJ>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
+          if (nvalid == L) item_df32<CGV, false, OBJ, MODEL>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
+          else item_df32<CGV, true, OBJ, MODEL>(s, cd, nA, lane, nvalid, tstart, t0d, hd, accv);
         } else {
-          if (nvalid == L) item_f32<CGV, false, OBJ>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
-          else item_f32<CGV, true, OBJ>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
+          if (nvalid == L) item_f32<CGV, false, OBJ, MODEL>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
+          else item_f32<CGV, true, OBJ, MODEL>(s, cd, nA, lane, nvalid, tstart, t0f, hf, accv);
         }
         const float z = warp_reduce_scatter<CGV>(accv, lane);
         if (owner) {

@@ -138,8 +138,8 @@ int admit(pt_serve_state* S, Slot& sl, Pending& p) {
   h.out = sl.d_out;
   const int sched[1] = {0}, off[2] = {0, 1};
   const int k = (int)std::max<int64_t>(1, std::min<int64_t>(h.blk.ntiles, S->ctas));
-  rc = launch_de_groups(w, sl.stream, full ? PT_TIER_F64 : p.req.tier, &h, 1, sched, off, 1, k, sl.d_desc,
-                        sl.d_ring, sl.d_err, DE_UPLOAD | DE_LAUNCH, full ? HOST_MODEL_FULL : HOST_MODEL_CUBIC);
+  rc = launch_de_groups(w, sl.stream, p.req.tier, &h, 1, sched, off, 1, k, sl.d_desc, sl.d_ring, sl.d_err,
+                        DE_UPLOAD | DE_LAUNCH, full ? HOST_MODEL_FULL : HOST_MODEL_CUBIC);
   if (rc != PT_OK) return rc;
   PT_CUDA(w, cudaMemcpyAsync(sl.h_out, sl.d_out, (dim + 1) * sizeof(double), cudaMemcpyDeviceToHost, sl.stream));
   PT_CUDA(w, cudaMemcpyAsync(sl.h_out + 8, sl.d_err, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
@@ -313,8 +313,7 @@ int pt_submit(pt_ctx* c, const pt_request* req, uint64_t* ticket) {
   double bnd[14];
   std::memcpy(bnd, b.bounds, sizeof(double) * 10);
   if (full) std::memcpy(bnd + 10, req->ext_bounds, sizeof(double) * 4);
-  int rc = check_de_args(c, bnd, b.pop, b.gens, b.F, b.CR, full ? PT_TIER_F64 : req->tier,
-                         full ? HOST_DMAX : HOST_D);
+  int rc = check_de_args(c, bnd, b.pop, b.gens, b.F, b.CR, req->tier, full ? HOST_DMAX : HOST_D);
   if (rc != PT_OK) return rc;
   const int obj = c->serve && c->serve->started ? c->serve->wctx.objective : c->objective;
   if (full && obj != PT_OBJ_CHI2) return fail(c, PT_EINVAL, "pt_submit: the full model runs on the chi-square only");

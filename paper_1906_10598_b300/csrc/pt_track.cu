@@ -130,7 +130,7 @@ int pt_track_block(pt_track* t, const void* samples, int64_t n, int dtype, doubl
     const uint64_t seed = c.seed + (uint64_t)(a - 1);
     if (full) {
       if ((rc = pt_de_solve_full(t->ctx, b, c.pop, c.gens, c.F, c.CR, seed, (uint32_t)t->next_index, p, nullptr,
-                                 nullptr)) != PT_OK)
+                                 nullptr, c.tier)) != PT_OK)
         return rc;
       sse = p[7];
     } else {

@@ -225,3 +225,32 @@ def test_de_full_population_extremes(ctx, pop):
     same = np.all(gpop == opop, axis=1)
     assert same.sum() >= pop - 1 and gpop.shape == (pop, 7)
     assert np.all(_rel(gfit[same], ofit[same]) <= 1e-6)
+
+
+@pytest.mark.parametrize("tier,tol", [("plain", 1e-9), ("df32", 1e-5), ("f32", None)])
+def test_objective_full_comparison_tiers(ctx, tier, tol):
+    # the all-FP64 tier (FP64 Horner in seconds, cospi), the double-float
+    # tier and the naive FP32 tier (reported, not bounded) on the full model
+    import paper_1906_10598_b300 as pt
+    blk = synth.perigee400k(12, n=40_000, storage=synth.F64)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    cands = np.vstack([_cands_in(blk.bounds, 23, 7), blk.truth[None, :]])
+    g = ctx.objective_full(cands, pt.TIERS[tier])
+    assert np.all(np.isfinite(g)) and np.all(g > 0)
+    if tol is not None:
+        o = oracle.sse_full_many(blk.values(), blk.fs, blk.t0, cands)
+        assert np.all(_rel(g, o) <= tol), float(np.max(_rel(g, o)))
+
+
+def test_de_full_plain_tier_bit_identical(ctx):
+    import paper_1906_10598_b300 as pt
+    blk = synth.perigee400k(13, n=6_000, storage=synth.F64)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    for gens in (0, 1, 6):
+        _, _, gpop, gfit = ctx.de_solve_full(blk.bounds, 32, gens, 0.7, 0.9, 41, return_population=True,
+                                             tier=pt.TIER_PLAIN)
+        _, _, opop, ofit = oracle.de_solve_full(blk.values(), blk.fs, blk.t0, blk.bounds, 32, gens, 0.7, 0.9, 41,
+                                                return_population=True)
+        same = np.all(gpop == opop, axis=1)
+        assert same.sum() >= 31, (gens, np.where(~same))
+        assert np.all(_rel(gfit[same], ofit[same]) <= 1e-9)
