@@ -127,3 +127,26 @@ def test_de_invalid_arguments(ctx):
     nanb[0, 0] = np.nan
     with pytest.raises(pt.PhaseTrackError):
         ctx.de_solve(nanb, 16, 5, 0.7, 0.9, 0)
+
+
+@pytest.mark.parametrize("model", ["cubic", "full"])
+def test_streamed_block_bit_identical(ctx, model):
+    # 8,000,000 int16 samples: 211 tiles per CTA, more than a CTA keeps in
+    # shared memory, so every generation stages its tiles chunk by chunk
+    import paper_1906_10598_b300 as pt
+    n = 8_000_000
+    blk = synth.paper400k(5, n=n) if model == "cubic" else synth.perigee400k(5, n=n)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    x = blk.values()
+    for gens in (0, 2):
+        if model == "cubic":
+            _, _, gpop, gfit = ctx.de_solve(blk.bounds, 16, gens, 0.7, 0.9, 5, pt.TIER_F64, return_population=True)
+            _, _, opop, ofit = oracle.de_solve(x, blk.fs, blk.t0, blk.bounds, 16, gens, 0.7, 0.9, 5,
+                                               return_population=True)
+        else:
+            _, _, gpop, gfit = ctx.de_solve_full(blk.bounds, 16, gens, 0.7, 0.9, 5, return_population=True)
+            _, _, opop, ofit = oracle.de_solve_full(x, blk.fs, blk.t0, blk.bounds, 16, gens, 0.7, 0.9, 5,
+                                                    return_population=True)
+        same = np.all(gpop == opop, axis=1)
+        assert same.sum() >= 15, (gens, np.where(~same))
+        assert np.all(np.abs(gfit[same] - ofit[same]) <= 1e-6 * ofit[same])
