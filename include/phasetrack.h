@@ -164,8 +164,8 @@ PT_API int pt_set_strategy(pt_ctx* ctx, int strategy);
  * Errors: PT_EINVAL, PT_ENOBLOCK, PT_ENOMEM, PT_ECUDA, PT_ETIMEOUT. */
 PT_API int pt_objective(pt_ctx* ctx, const double* cands, int64_t n, double* sse_out, int tier);
 
-/* Fit the loaded block by DE/rand/1/bin (Sec. 1.2, Table 3-1-1) in one
- * persistent device launch.
+/* Fit the loaded block by DE (Sec. 1.2, Table 3-1-1; the context's strategy,
+ * DE/rand/1/bin by default, and objective) in one persistent device launch.
  *   bounds      host pointer, 5 x 2 doubles: (lo, hi) per parameter. The phi0
  *               range wraps when it spans a full circle (Sec. 3.1.1: [0, 2 pi]);
  *               other out-of-range trial components move to the midpoint of

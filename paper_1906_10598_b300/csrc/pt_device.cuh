@@ -240,8 +240,7 @@ __device__ __forceinline__ double half_exact(double x) {
   return (e > 1 && e < 0x7FF) ? __longlong_as_double(b - (1ll << 52)) : __dmul_rn(x, 0.5);
 }
 
-// Component j of the DE/rand/1/bin trial of individual i from population x
-// (np x DIM). FP64 operations use _rn intrinsics so no contraction changes a
+// Component j of the DE trial of individual i from population x (np x DIM). FP64 operations use _rn intrinsics so no contraction changes a
 // rounding: the value is bit-identical to a plain IEEE evaluation.
 // STRAT is the DE_* strategy (a template parameter, so each strategy's loop
 // holds only its own FP64 operations); `best` (the previous generation's

@@ -2,7 +2,7 @@
 //   k_absmax      max |stored sample| of a loaded block (sets the SSE fixed-point scale)
 //   k_objective   Eq. 2-2-4 for a fixed candidate set (tiles x candidate batches)
 //   k_finalize    fixed-point accumulators -> FP64 SSE
-//   k_de          persistent DE/rand/1/bin solve of one block (Table 3-1-1 controls)
+//   k_de          persistent DE solve of a group's blocks (Table 3-1-1 controls and strategies)
 //
 // Work decomposition shared by the objective and DE kernels: a CTA owns a
 // contiguous range of 256-sample tiles, staged once into shared memory by a
@@ -134,7 +134,7 @@ __device__ __forceinline__ void prep_zero(unsigned char* cdata, float* negA, int
   for (int k = 0; k < cand_bytes(MODEL) / 16; ++k) p[k] = make_uint4(0, 0, 0, 0);
 }
 
-// Prepare candidates [0, nc) of `cands` (rows of 5 doubles) padded to npad.
+// Prepare candidates [0, nc) of `cands` (rows of model_dim(MODEL) doubles) padded to npad.
 // The default tier spreads the four FP64 polynomial terms and the amplitude
 // over separate threads so the 1/64-rate FP64 work is spread across all
 // warps of the CTA, and flags in cub[c] the candidates whose cubic term must
@@ -868,7 +868,7 @@ __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& s
   }
 }
 
-// DE/rand/1/bin on one block by `k` CTAs (this one is `rank`). Every CTA holds
+// DE (the block's strategy) on one block by `k` CTAs (this one is `rank`). Every CTA holds
 // the whole population and generates every trial itself (identical Philox
 // draws, identical FP64 arithmetic), so the only exchange is each trial's SSE:
 // every CTA adds (partial << 8) | 1 to the trial's 64-bit word of the group's
@@ -877,7 +877,7 @@ __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& s
 // replaces a barrier, a fence and a separate read. `gg` counts the group's
 // generations across blocks so the ring discipline continues from block to
 // block. Returns false if a bounded wait expired or another CTA failed.
-// MODEL_FULL: the full model's 7 parameters (default tier, chi-square).
+// MODEL_FULL: the full model's 7 parameters (chi-square).
 template <int TIER, int CGV, int OBJ, int MODEL = MODEL_CUBIC>
 __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long long* ring, unsigned long long& gg,
                          const DeSmem& sm, const DeLaunch& a, int* s_abort) {
