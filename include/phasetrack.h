@@ -480,7 +480,11 @@ typedef struct pt_track_result {
 
 /* Start a session on ctx (which it uses for every fit; one session per
  * context at a time). bounds: the first block's (lo, hi) pairs for A, phi0,
- * f0, f1, f2 (host pointer, 10 doubles). Errors: PT_EINVAL, PT_ENOMEM. */
+ * f0, f1, f2 (host pointer, 10 doubles), lo <= hi; a parameter whose range is
+ * a point (lo == hi) stays at that value in every search of the session (the
+ * constant amplitude of the correlation objective, Eq. 2-2-6, or f3 = 0 for
+ * the paper's 6-parameter model in a full-model session).
+ * Errors: PT_EINVAL, PT_ENOMEM. */
 PT_API int pt_track_create(pt_ctx* ctx, const pt_track_config* cfg, const double bounds[10], pt_track** out);
 
 /* A session that fits every block with the full model (pt_de_solve_full:

@@ -33,10 +33,19 @@ double wrap_2pi(double x) {
   return r < 0.0 ? r + TWO_PI_D : r;
 }
 
+// Finite (lo, hi) pairs with lo <= hi (lo == hi holds the parameter fixed).
 bool finite_bounds(const double* b, int dim) {
   for (int j = 0; j < dim; ++j)
-    if (!std::isfinite(b[2 * j]) || !std::isfinite(b[2 * j + 1]) || !(b[2 * j] < b[2 * j + 1])) return false;
+    if (!std::isfinite(b[2 * j]) || !std::isfinite(b[2 * j + 1]) || !(b[2 * j] <= b[2 * j + 1])) return false;
   return true;
+}
+
+// A parameter whose initial range is a point stays there in every search
+// (e.g. f3 = 0 for the paper's 6-parameter model, or the constant amplitude
+// of the correlation objective, Eq. 2-2-6).
+void keep_fixed(double* b, const double* init, int dim) {
+  for (int j = 0; j < dim; ++j)
+    if (init[2 * j] == init[2 * j + 1]) b[2 * j] = b[2 * j + 1] = init[2 * j];
 }
 
 // Widen the f0, f1, f2 and A ranges (and the full model's f3) about their
@@ -76,8 +85,6 @@ int create_session(pt_ctx* ctx, const pt_track_config* cfg, const double* bounds
       !(cfg->CR >= 0.0) || !std::isfinite(cfg->CR) || !valid_tier(cfg->tier) || !(cfg->max_dphi > 0.0) ||
       !(cfg->max_dfreq > 0.0) || !(cfg->enlarge >= 1.0) || !std::isfinite(cfg->enlarge) ||
       cfg->max_attempts < 1 || std::isnan(cfg->count_interval) || !finite_bounds(bounds, dim))
-    return fail(ctx, PT_EINVAL, "pt_track_create: invalid configuration or bounds");
-  if (dim == 7 && (bounds[10] > bounds[11] || bounds[12] > bounds[13]))
     return fail(ctx, PT_EINVAL, "pt_track_create: invalid configuration or bounds");
   pt_track* t = new (std::nothrow) pt_track;
   if (!t) return fail(ctx, PT_ENOMEM, "pt_track_create: out of host memory");
@@ -121,6 +128,7 @@ int pt_track_block(pt_track* t, const void* samples, int64_t n, int dtype, doubl
   } else if ((rc = pt_warm_bounds(t->ref, t->ref_to_end + 0.5 * T, T, 0.0, 0.0, 0.0, b)) != PT_OK) {
     return rc;
   }
+  keep_fixed(b, t->init, t->dim);
   double p[8] = {};  // (A, phi0, f0, f1, f2, A1, f3) and the SSE; A1 = f3 = 0 for the cubic model
   double sse = 0.0;
   double dphi = NaN, dfreq = NaN;
@@ -153,7 +161,10 @@ int pt_track_block(pt_track* t, const void* samples, int64_t n, int dtype, doubl
       quality = a;
       break;
     }
-    if (a < c.max_attempts) enlarge_bounds(b, c.enlarge, t->dim);
+    if (a < c.max_attempts) {
+      enlarge_bounds(b, c.enlarge, t->dim);
+      keep_fixed(b, t->init, t->dim);
+    }
   }
   pt_track_result r{};
   r.block_index = t->next_index++;

@@ -213,3 +213,31 @@ def test_full_model_tracker_refuses_other_settings(ctx):
     tr.close()
     with pytest.raises(ValueError):
         pt.Tracker(ctx, bounds[:6], pop=16, gens=10)
+
+
+def test_fixed_parameters_stay_fixed_through_the_session(ctx):
+    # the paper's 6-parameter model in a full-model session (f3 held at 0), and
+    # a correlation-objective session with its constant amplitude (Eq. 2-2-6)
+    import paper_1906_10598_b300 as pt
+    sp = _stream()
+    b0 = synth.stream_block(sp, 0)
+    full_bounds = np.vstack([b0.bounds, [[-0.01, 0.01], [0.0, 0.0]]])
+    tr = pt.Tracker(ctx, full_bounds, pop=32, gens=300, seed=1, max_dphi=0.3, max_dfreq=2 * math.pi)
+    for k in range(3):
+        b = synth.stream_block(sp, k)
+        r = tr.block(b.samples, b.fs, b.scale)
+        assert r["quality"] == 1 and r["params"][6] == 0.0 and abs(r["params"][2] - b.truth[2]) < 0.05
+    tr.close()
+    cor_bounds = b0.bounds.copy()
+    cor_bounds[0] = (b0.truth[0], b0.truth[0])
+    ctx.set_objective("cor")
+    try:
+        tr = pt.Tracker(ctx, cor_bounds, pop=32, gens=300, seed=2, max_dphi=0.3, max_dfreq=2 * math.pi)
+        for k in range(3):
+            b = synth.stream_block(sp, k)
+            r = tr.block(b.samples, b.fs, b.scale)
+            assert r["quality"] >= 1 and r["params"][0] == b0.truth[0]
+            assert abs(r["params"][2] - b.truth[2]) < 0.05
+        tr.close()
+    finally:
+        ctx.set_objective("chi2")
