@@ -317,13 +317,15 @@ def run_batch(args):
     """256 independent blocks of uneven length (N log-uniform 50K-1M int16, fs 1-50
     kHz, pop 32-128, G = ceil(80000/pop)) in one persistent launch under a CUDA
     graph, launch shape chosen by the autotuner. Compared with the all-FP64
-    single-block form on a sample of the same blocks."""
+    single-block form on a sample of the same blocks. With --model full: the
+    same shapes for the full model (synth.batch_full)."""
     import torch
     import oracle
     import paper_1906_10598_b300 as pt
     from paper_1906_10598_b300 import build
     build.build()
-    blocks = synth.batch(0, nblocks=args.nblocks)
+    full = args.model == "full"
+    blocks = synth.batch_full(0, nblocks=args.nblocks) if full else synth.batch(0, nblocks=args.nblocks)
     ctx = pt.Context(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -350,7 +352,7 @@ def run_batch(args):
     rel = []
     for i in range(0, len(blocks), max(1, len(blocks) // 4)):
         b = blocks[i]
-        want = oracle.sse(b.values(), b.fs, b.t0, params[i])
+        want = (oracle.sse_full if full else oracle.sse)(b.values(), b.fs, b.t0, params[i])
         rel.append(abs(sse[i] - want) / want)
     # all-FP64 single-block form on a sample of the blocks (one pt_de_solve each)
     order = np.argsort([b.n for b in blocks])
@@ -359,9 +361,10 @@ def run_batch(args):
     for i in sample_ids:
         b = blocks[i]
         ctx.load_block(b.samples, b.fs, b.t0, b.scale)
-        ctx.de_solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, pt.TIER_PLAIN, block_id=b.block_id)
+        solve = ctx.de_solve_full if full else ctx.de_solve
+        solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, block_id=b.block_id, tier=pt.TIER_PLAIN)
         plain_s += ctx.last_kernel_ms() * 1e-3
-        ctx.de_solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, pt.TIER_F64, block_id=b.block_id)
+        solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, block_id=b.block_id, tier=pt.TIER_F64)
         fast_s += ctx.last_kernel_ms() * 1e-3
         plain_evals += b.sample_evals()
     plain_rate = plain_evals / plain_s
@@ -379,7 +382,8 @@ def run_batch(args):
     line = {"metric": "batched objective sample-evals/s", "value": evals / mean_s, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batch{len(blocks)}_int16_n50k-1m_pop32-128", "blocks": len(blocks),
+            "config": {"workload": f"batch{len(blocks)}_int16_n50k-1m_pop32-128" + ("_full_model" if full else ""),
+                       "model": "full" if full else "cubic", "blocks": len(blocks),
                        "total_samples": int(sum(b.n for b in blocks)), "l2": "flushed between steps",
                        "group_ctas": info["group_ctas"], "groups": info["ngroups"],
                        "uses_graph": info["uses_graph"], "autotune_predicted_ms": info["predicted_ms"],
@@ -388,7 +392,8 @@ def run_batch(args):
             "blocks_per_s": len(blocks) / mean_s,
             "roofline": {"bound": "alu", "achieved": evals / mean_s, "peak": SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6,
                          "unit": UNIT, "frac": evals / mean_s / (SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6),
-                         "traffic": None, "kernel": "k_de<TIER_F64> (grouped)"},
+                         "traffic": None,
+                         "kernel": "k_de<TIER_F64, OBJ_CHI2, MODEL_FULL> (grouped)" if full else "k_de<TIER_F64> (grouped)"},
             "plain_f64_single_block": {"sample_evals_per_s": plain_rate,
                                        "blocks_per_s_est": len(blocks) / (evals / plain_rate),
                                        "sampled_blocks": sample_ids,
@@ -396,7 +401,7 @@ def run_batch(args):
             "fit_sse_rel_err_vs_oracle_max": float(max(rel)),
             "clocks": clocks, "gpu_launches": args.steps,
             "e2e": {"value": evals / float(np.mean(e2e)), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": len(blocks) * 48}}
+                    "d2h_bytes_per_step": len(blocks) * 64}}
     print(json.dumps(line))
     batch.close()
     ctx.close()

@@ -245,6 +245,42 @@ def batch(seed: int = 0, nblocks: int = 256, n_lo: int = 50_000, n_hi: int = 1_0
     return out
 
 
+def batch_full(seed: int = 0, nblocks: int = 256, n_lo: int = 50_000, n_hi: int = 1_000_000, fs_lo: float = 1_000.0,
+               fs_hi: float = 50_000.0, evals: int = 80_000) -> List[Block]:
+    """The `batch` workload for the full model: the same block lengths, rates and
+    populations, each tone with an amplitude slope A1 ~ U(-0.1, 0.1) A / T and a
+    quartic term f3 ~ U(-1, 1) f3_max, f3_max = min(5e-4, 2.4 fs / T^3) cycles/s^4
+    (the quartic's frequency excursion over the block stays within 5 % of fs);
+    7 x 2 bounds: the `paper400k` windows, A1 over +-0.2 A / T, f3 +- 192 / T^4."""
+    rng = np.random.Generator(np.random.PCG64(seed + 5_000_011))
+    out = []
+    for b in range(nblocks):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        fs = float(math.exp(rng.uniform(math.log(fs_lo), math.log(fs_hi))))
+        T = n / fs
+        f1_max = min(5.0, 0.1 * fs / T)
+        f2_max = min(0.05, 0.4 * fs / T ** 2)
+        f3_max = min(5e-4, 2.4 * fs / T ** 3)
+        A = rng.uniform(0.5, 2.0)
+        truth = np.array([A, rng.uniform(-math.pi, math.pi), rng.uniform(-0.4 * fs, 0.4 * fs),
+                          rng.uniform(-f1_max, f1_max), rng.uniform(-f2_max, f2_max),
+                          rng.uniform(-0.1, 0.1) * A / T, rng.uniform(-f3_max, f3_max)])
+        snr_db = rng.uniform(0.0, 30.0)
+        sigma = _sigma_for(A, snr_db)
+        t0 = centred_t0(n, fs)
+        x = clean_tone_full(truth, n, fs, t0) + rng.normal(0.0, sigma, n)
+        bounds = np.zeros((7, 2))
+        bounds[:5] = paper_bounds(rng, truth[:5], T)
+        bounds[5] = (-0.2 * bounds[0, 1] / T, 0.2 * bounds[0, 1] / T)
+        bounds[6] = _window(rng, truth[6], 192.0 / T ** 4)
+        stored, scale = quantise(x, A * 1.1 + 6.0 * sigma, I16)
+        pop = int(rng.integers(32, 129))
+        gens = int(math.ceil(evals / pop))
+        out.append(Block(stored, I16, scale, fs, t0, truth, sigma, snr_db, bounds, pop=pop, gens=gens, F=0.7,
+                         CR=0.9, de_seed=seed * 1000 + b, block_id=b, noise=None))
+    return out
+
+
 @dataclasses.dataclass
 class StreamSpec:
     """One simulated station stream with a continuous phase
