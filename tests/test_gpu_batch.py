@@ -106,3 +106,24 @@ def test_full_model_batch_bit_identical_to_single_solves(ctx):
     # the cubic and full models do not mix in one batch
     with pytest.raises(ValueError):
         pt.Batch(ctx, [blocks[0], synth.paper400k(1, n=1000, gens=3)])
+
+
+@pytest.mark.parametrize("strategy", ["best1jitter", "eitheror"])
+def test_batch_strategies_bit_identical_to_single_solves(ctx, strategy):
+    import paper_1906_10598_b300 as pt
+    blocks = _mixed_blocks()[:5]
+    ctx.set_strategy(strategy)
+    try:
+        alone = []
+        for b in blocks:
+            ctx.load_block(b.samples, b.fs, b.t0, b.scale)
+            alone.append(ctx.de_solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, pt.TIER_F64,
+                                      block_id=b.block_id))
+        batch = pt.Batch(ctx, blocks, pt.TIER_F64, group_ctas=4)
+        batch.run()
+        params, sse = batch.results()
+        for i, (p1, s1) in enumerate(alone):
+            assert np.array_equal(params[i], p1) and sse[i] == s1, i
+        batch.close()
+    finally:
+        ctx.set_strategy("rand1bin")
