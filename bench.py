@@ -706,6 +706,8 @@ def run_precision(args):
     import paper_1906_10598_b300 as pt
     from paper_1906_10598_b300 import build
     build.build()
+    if args.model == "full":
+        return run_precision_full(args)
     ref_path = os.path.join(ROOT, "tests", "golden", "precision_oracle_fits.json")
     ref = json.load(open(ref_path)) if os.path.exists(ref_path) else {}
     ctx = pt.Context(0)
@@ -751,6 +753,53 @@ def run_precision(args):
             e["within_1e-3rad_1e-5Hz_of_oracle_in_basin"] = float(np.mean(ok)) if ok else None
         table.append(e)
     print(json.dumps({"metric": "precision sweep", "workload": "paper400k x storage x tier", "rows": table}))
+    ctx.close()
+    return 0
+
+
+def run_precision_full(args):
+    """Precision of the full model's tiers on the perigee-shaped 400K block
+    (int8 / FP16 / FP32 storage, `--seeds` seeds, 8 by default here): the
+    objective's relative error against the oracle's SSE at each tier's fitted
+    parameters, and the fits' phi0 / f0 / f3 errors against the truth (the
+    full model has no stored oracle fits: each takes the oracle minutes)."""
+    import oracle
+    import paper_1906_10598_b300 as pt
+    ctx = pt.Context(0)
+    tiers = {"f64-anchored": pt.TIER_F64, "all-f64": pt.TIER_PLAIN, "double-float": pt.TIER_DF32,
+             "naive-f32": pt.TIER_F32}
+    seeds = min(args.seeds, 8)
+    rows = {}
+    for st in ("i8", "f16", "f32"):
+        for seed in range(seeds):
+            b = synth.perigee400k(seed, storage=synth.STORAGE_NAMES[st])
+            ctx.load_block(b.samples, b.fs, b.t0, b.scale)
+            vals = b.values()
+            sse_truth = oracle.sse_full(vals, b.fs, b.t0, b.truth)
+            for name, tier in tiers.items():
+                p, f = ctx.de_solve_full(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, tier=tier)
+                ms = ctx.last_kernel_ms()
+                want = oracle.sse_full(vals, b.fs, b.t0, p)
+                d = rows.setdefault((st, name), {"sse_rel": [], "ms": [], "dphi0": [], "df0": [], "df3": [],
+                                                 "at_or_below_truth": []})
+                d["sse_rel"].append(abs(f - want) / want)
+                d["ms"].append(ms)
+                d["dphi0"].append(abs(float(np.angle(np.exp(1j * (p[1] - b.truth[1]))))))
+                d["df0"].append(abs(p[2] - b.truth[2]))
+                d["df3"].append(abs(p[6] - b.truth[6]))
+                d["at_or_below_truth"].append(want <= sse_truth * (1 + 1e-6))
+    table = []
+    for (st, name), d in rows.items():
+        table.append({"storage": st, "tier": name, "seeds": len(d["sse_rel"]),
+                      "sse_rel_err_max": float(np.max(d["sse_rel"])),
+                      "sse_rel_err_median": float(np.median(d["sse_rel"])),
+                      "fit_ms_median": float(np.median(d["ms"])),
+                      "phi0_err_vs_truth_median": float(np.median(d["dphi0"])),
+                      "f0_err_vs_truth_hz_median": float(np.median(d["df0"])),
+                      "f3_err_vs_truth_median": float(np.median(d["df3"])),
+                      "fits_at_or_below_truth_sse": float(np.mean(d["at_or_below_truth"]))})
+    print(json.dumps({"metric": "precision sweep (full model)", "workload": "perigee400k x storage x tier",
+                      "rows": table}))
     ctx.close()
     return 0
 
