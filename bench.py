@@ -80,22 +80,41 @@ def kernel_sources_sha256() -> str:
     return h.hexdigest()
 
 
+def _profile_fields(path: str):
+    fields = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.startswith(("traffic_bytes_per_launch", "kernel_sources_sha256",
+                                                "fp64_pipe_pct_of_peak")):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+    return fields
+
+
 def profiled_traffic(path: str = PROFILE):
     """(DRAM bytes per launch, note) from the committed ncu summary, or (None,
     why) when the kernel sources changed since that capture."""
     try:
-        fields = {}
-        with open(path) as fh:
-            for line in fh:
-                if ":" in line and line.startswith(("traffic_bytes_per_launch", "kernel_sources_sha256")):
-                    k, v = line.split(":", 1)
-                    fields[k.strip()] = v.strip().strip("`")
+        fields = _profile_fields(path)
         if fields.get("kernel_sources_sha256") != kernel_sources_sha256():
             return None, "kernel sources changed since the ncu capture"
         return int(fields["traffic_bytes_per_launch"]), "ncu dram__bytes_read + write, one launch (" + \
             os.path.basename(path) + ")"
     except (OSError, KeyError, ValueError):
         return None, "no ncu summary"
+
+
+def profiled_fp64_share(path: str = PROFILE):
+    """The FP64 pipe's share of its peak over one launch (the DE's trial
+    generation and phase set-up, counted apart from the SFU roofline) from the
+    committed ncu summary, or None when the kernel sources changed since."""
+    try:
+        fields = _profile_fields(path)
+        if fields.get("kernel_sources_sha256") != kernel_sources_sha256():
+            return None
+        return float(fields["fp64_pipe_pct_of_peak"]) / 100.0
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def _dist():
@@ -177,9 +196,18 @@ def cpu_baseline(blk: synth.Block, gens: int = 240, full: bool = False):
     solve(s, blk.fs, blk.t0, blk.bounds, blk.pop, gens, blk.F, blk.CR, blk.de_seed, nthreads=cores)
     dt = time.perf_counter() - t
     evals = blk.n * blk.pop * (gens + 1)
+    # and on one core, on a shorter sample (the paper's single-thread baseline)
+    g1 = max(1, gens // 15)
+    t = time.perf_counter()
+    solve(s, blk.fs, blk.t0, blk.bounds, blk.pop, g1, blk.F, blk.CR, blk.de_seed, nthreads=1)
+    dt1 = time.perf_counter() - t
+    evals1 = blk.n * blk.pop * (g1 + 1)
     return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"oracle DE{' (full model)' if full else ''} on the 400K int16 block, pop {blk.pop}, "
-                      f"{gens} generations ({evals:.3g} sample-evals, {dt:.1f} s)"}
+                      f"{gens} generations ({evals:.3g} sample-evals, {dt:.1f} s)",
+            "one_core": {"value": evals1 / dt1, "unit": UNIT, "cores": 1,
+                         "sample": f"the same DE for {g1} generations on one thread ({evals1:.3g} sample-evals, "
+                                   f"{dt1:.1f} s)"}}
 
 
 def run_reference(args):
@@ -288,6 +316,8 @@ def run_gpu(args):
             "peak_basis": "148 SMs x 16 SFU cosines/clk x 2032 MHz (one cosine per sample-eval)"}
     if clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (SMS * SFU_PER_CLK * clocks["sm_mhz"] * 1e6)
+    roof["fp64_pipe_share"] = profiled_fp64_share(PROFILE_FULL_MODEL if full else PROFILE)
+    roof["fp64_pipe_note"] = "ncu sm__inst_executed_pipe_fp64 % of peak over one launch (trial generation, set-up)"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": value / world / PAPER_SAMPLE_EVALS_PER_S, "dtype": "f32",
