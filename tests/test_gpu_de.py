@@ -60,6 +60,26 @@ def test_early_generations_bit_identical(ctx, tier_name):
         assert np.all(np.abs(gfit[same] - ofit[same]) <= tol * ofit[same])
 
 
+@pytest.mark.parametrize("pop", [4, 17, 128])
+@pytest.mark.parametrize("tier_name", ["plain", "f64"])
+def test_early_generations_population_edges(ctx, tier_name, pop):
+    # pop 4: the three donors are exactly the other members; 17: a ragged last
+    # candidate group; 128: the largest population (eight 16-wide groups)
+    import paper_1906_10598_b300 as pt
+    blk = synth.single4096(5)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    for gens in (1, 5):
+        _, _, gpop, gfit = ctx.de_solve(blk.bounds, pop, gens, 0.7, 0.9, 31, pt.TIERS[tier_name],
+                                        return_population=True)
+        _, _, opop, ofit = oracle.de_solve(blk.values(), blk.fs, blk.t0, blk.bounds, pop, gens, 0.7, 0.9, 31,
+                                           return_population=True)
+        assert gpop.shape == opop.shape == (pop, 5)
+        same = np.all(gpop == opop, axis=1)
+        assert same.sum() >= pop - 1, (gens, np.where(~same))
+        tol = 1e-9 if tier_name == "plain" else 1e-6
+        assert np.all(np.abs(gfit[same] - ofit[same]) <= tol * ofit[same])
+
+
 def test_single4096_plain_fit_matches_oracle(ctx):
     # the N = 4096 FP64 block, pop 32, 200 generations, F 0.7, CR 0.9, seed 0, FP64 plain method
     import paper_1906_10598_b300 as pt
