@@ -64,6 +64,28 @@ def test_early_generations_bit_identical(ctx, strategy, objective, tier):
         ctx.set_objective("chi2")
 
 
+@pytest.mark.parametrize("pop", [4, 128])
+@pytest.mark.parametrize("strategy", ["best1jitter", "eitheror"])
+def test_strategy_population_edges(ctx, strategy, pop):
+    # pop 4: the donors are exactly the other three members (for "3" the best
+    # member may be one of them); pop 128: the largest population
+    import paper_1906_10598_b300 as pt
+    blk = synth.single4096(6)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    ctx.set_strategy(strategy)
+    try:
+        for gens in (1, 5):
+            _, _, gpop, gfit = ctx.de_solve(blk.bounds, pop, gens, 0.7, 0.9, 45, pt.TIER_PLAIN,
+                                            return_population=True)
+            _, _, opop, ofit = oracle.de_solve(blk.values(), blk.fs, blk.t0, blk.bounds, pop, gens, 0.7, 0.9, 45,
+                                               return_population=True, strategy=strategy)
+            same = np.all(gpop == opop, axis=1)
+            assert same.sum() >= pop - 1, (gens, np.where(~same))
+            assert np.all(np.abs(gfit[same] - ofit[same]) <= 1e-9 * ofit[same])
+    finally:
+        ctx.set_strategy("rand1bin")
+
+
 @pytest.mark.parametrize("strategy,objective", [("best1jitter", "chi2"), ("eitheror", "cor")])
 def test_strategy_fit_matches_oracle(ctx, strategy, objective):
     # the paper's pairings (Sec. 3.1.2): "3" with Eq. 2-2-4, "6" with Eq. 2-2-5.
