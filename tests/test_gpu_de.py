@@ -60,6 +60,30 @@ def test_early_generations_bit_identical(ctx, tier_name):
         assert np.all(np.abs(gfit[same] - ofit[same]) <= tol * ofit[same])
 
 
+@pytest.mark.parametrize("n", [1, 255, 256, 257])
+@pytest.mark.parametrize("tier_name", ["plain", "f64"])
+def test_early_generations_short_blocks(ctx, tier_name, n):
+    # one sample; one tile short of, exactly, and one sample past a 256-sample
+    # tile (the ragged tile's masked samples, a tile of one sample)
+    import paper_1906_10598_b300 as pt
+    blk = synth.single4096(7, n=n)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    s = blk.values()
+    for gens in (1, 4):
+        _, _, gpop, gfit = ctx.de_solve(blk.bounds, 16, gens, 0.7, 0.9, 3, pt.TIERS[tier_name],
+                                        return_population=True)
+        _, _, opop, ofit = oracle.de_solve(s, blk.fs, blk.t0, blk.bounds, 16, gens, 0.7, 0.9, 3,
+                                           return_population=True)
+        same = np.all(gpop == opop, axis=1)
+        assert same.sum() >= 15, (gens, np.where(~same))
+        # the relative target plus the propagation of a per-sample residual
+        # error, which dominates when one or a few samples leave a small SSE
+        rel, dr = (1e-9, 1e-12) if tier_name == "plain" else (1e-6, 2e-6)
+        dr *= float(np.max(np.abs(s))) + float(np.max(np.abs(gpop[:, 0])))
+        o = ofit[same]
+        assert np.all(np.abs(gfit[same] - o) <= rel * o + 2.0 * np.sqrt(n * o) * dr + n * dr * dr)
+
+
 @pytest.mark.parametrize("pop", [4, 17, 128])
 @pytest.mark.parametrize("tier_name", ["plain", "f64"])
 def test_early_generations_population_edges(ctx, tier_name, pop):
