@@ -55,6 +55,29 @@ def test_batch_bit_identical_to_single_solves(ctx):
         batch.close()
 
 
+def test_batch_degenerate_blocks_bit_identical_to_single_solves(ctx):
+    # a one-sample block at the smallest population, a block of exactly one
+    # tile, and a small block at the largest population, in one launch
+    import paper_1906_10598_b300 as pt
+    blocks = []
+    for i, (n, pop) in enumerate([(1, 4), (256, 5), (3000, 128)]):
+        b = synth.paper400k(200 + i, n=n, fs=2_000.0, pop=pop, gens=12)
+        b.block_id = 40 + i
+        b.de_seed = 3 + i
+        blocks.append(b)
+    alone = []
+    for b in blocks:
+        ctx.load_block(b.samples, b.fs, b.t0, b.scale)
+        alone.append(ctx.de_solve(b.bounds, b.pop, b.gens, b.F, b.CR, b.de_seed, pt.TIER_F64, block_id=b.block_id))
+    for k in (0, 2):
+        batch = pt.Batch(ctx, blocks, pt.TIER_F64, group_ctas=k)
+        batch.run()
+        params, sse = batch.results()
+        for i, (p1, s1) in enumerate(alone):
+            assert np.array_equal(params[i], p1) and sse[i] == s1, (k, i)
+        batch.close()
+
+
 def test_batch_fits_match_oracle_objective(ctx):
     import paper_1906_10598_b300 as pt
     blocks = synth.batch(3, nblocks=6, n_lo=20_000, n_hi=80_000, evals=6_000)
