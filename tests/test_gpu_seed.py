@@ -32,10 +32,12 @@ def _blocks():
     out = [synth.single4096(s) for s in range(3)]
     out += [synth.paper400k(s, n=n) for s, n in ((0, 400_000), (1, 100_003), (2, 33_333))]
     out += [synth.paper400k(3, n=50_000, storage=synth.I8), synth.perigee400k(1, n=80_000)]
+    # the shortest blocks: pieces of 16, 16 and 32 samples
+    out += [synth.single4096(s, n=n) for s, n in ((4, 64), (5, 127), (6, 255))]
     return out
 
 
-@pytest.mark.parametrize("i", range(8))
+@pytest.mark.parametrize("i", range(11))
 def test_seed_matches_oracle(ctx, i):
     blk = _blocks()[i]
     ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
