@@ -117,6 +117,45 @@ def profiled_fp64_share(path: str = PROFILE):
         return None
 
 
+def measure_pipes(device: int, full: bool = True) -> dict:
+    """The pipe microbenchmarks (pt_pipe_rate) on `device`: the pure __cosf
+    rate (the objective's roofline denominator), __cosf with 2, 4, 6 and 8 FP32
+    FMAs each, FP32 FMAs alone (the issue rate) and FP64 FMAs alone. Per SM
+    clock per SM and per second."""
+    import paper_1906_10598_b300 as pt
+    out = {"cos": pt.pipe_rate(device, pt.PIPE_COS, 0), "ffma": pt.pipe_rate(device, pt.PIPE_FFMA)}
+    if full:
+        for nf in (2, 4, 6, 8):
+            out[f"cos_{nf}ffma"] = pt.pipe_rate(device, pt.PIPE_COS, nf)
+        out["dfma"] = pt.pipe_rate(device, pt.PIPE_DFMA)
+        out["ex2"] = pt.pipe_rate(device, pt.PIPE_EX2)
+    return out
+
+
+def run_peaks(args):
+    """The pipe rates of this GPU (pt_pipe_rate) with the clocks sampled while
+    they run: the denominators of the objective's roofline."""
+    from paper_1906_10598_b300 import build
+    build.build()
+    sampler = ClockSampler(0)
+    sampler.start()
+    rates = measure_pipes(0, full=True)
+    clocks = sampler.stop()
+    sms = _sm_count()
+    line = {"metric": "pipe rates", "sms": sms, "rates": rates, "clocks": clocks,
+            "cos_per_clk_sm": rates["cos"]["per_clk_sm"],
+            "warp_inst_per_clk_sm": rates["ffma"]["per_clk_sm"] / 32.0,
+            "dfma_per_clk_sm": rates["dfma"]["per_clk_sm"],
+            "sfu_peak_sample_evals_per_s_at_max_clock": rates["cos"]["per_clk_sm"] * sms * SM_MAX_MHZ * 1e6}
+    print(json.dumps(line))
+    return 0
+
+
+def _sm_count() -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(0).multi_processor_count)
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -846,7 +885,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--mode", default="single",
-                    choices=["single", "batch", "serve", "precision", "track", "objective", "seed"],
+                    choices=["single", "batch", "serve", "precision", "track", "objective", "seed", "peaks"],
                     help="single: the 400K-block fit (default); batch: 256 uneven blocks in one launch; "
                          "serve: 4 station streams through pt_submit/pt_poll; track: one stream through pt_track")
     ap.add_argument("--track-blocks", type=int, default=60, help="track: blocks of the tracked stream")
@@ -878,6 +917,8 @@ def main():
         return run_precision(args)
     if args.mode == "seed":
         return run_seed(args)
+    if args.mode == "peaks":
+        return run_peaks(args)
     return run_gpu(args)
 
 

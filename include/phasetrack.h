@@ -517,15 +517,24 @@ PT_API void pt_track_destroy(pt_track* tr);
  *     (PT_NOALLOC_MAX_CANDIDATES + 32 64-bit words, about 33 KB), which every
  *     GPU that loads the library holds until the process exits.
  * Arguments:
- *   samples   device pointer to ceil(n/256)*256 readable values of type dtype
- *             (values past n are read and ignored).
+ *   samples   device pointer, 16-byte aligned, to ceil(n/256)*256 readable
+ *             values of type dtype inside one allocation (values past n are
+ *             read and ignored): the tiles are staged by bulk copies that need
+ *             16-byte-aligned sources and read whole 256-sample tiles.
  *   n, dtype, scale, fs, t0  as in pt_load_block.
  *   smax      an upper bound on |scale * sample|; 0 takes the type's range
  *             (128, 32768, 65504 times scale for I8, I16, F16). F32 and F64
- *             samples need an explicit bound.
- *   cands     device pointer, ncand rows of 5 doubles (A, phi0, f0, f1, f2).
+ *             samples need an explicit bound. The per-tile sums are fixed
+ *             point scaled so that n (smax + |A|)^2 fits 61 bits, so a loose
+ *             bound coarsens them: pass a tight one (the type's range is
+ *             tight for integer samples quantised to their full range, not
+ *             for FP16 samples of a few units).
+ *   cands     device pointer, 8-byte aligned, ncand rows of 5 doubles (A, phi0,
+ *             f0, f1, f2) inside one allocation.
  *   ncand     1 <= ncand <= PT_NOALLOC_MAX_CANDIDATES; larger is PT_EINVAL.
- *   sse_out   device pointer, ncand doubles.
+ *   sse_out   device pointer, 8-byte aligned, ncand doubles inside one
+ *             allocation.
+ * Every buffer must be memory of the current device (or managed memory).
  *   tier      PT_TIER_*.
  *   stream    cudaStream_t to launch on (NULL: the legacy default stream).
  * The call is synchronous on `stream`. The first call on a device looks up
@@ -534,12 +543,39 @@ PT_API void pt_track_destroy(pt_track* tr);
  * scratch before use (the array keeps the previous call's contents); calls
  * whose work overlaps on the GPU share the one array and race, so callers must
  * serialise them (one stream, or one call at a time per device).
- * Errors: PT_EINVAL (sizes, pointers that are not device memory, a missing
- * bound), PT_ECUDA, PT_ETIMEOUT. */
+ * Errors: PT_EINVAL (sizes; a pointer that is not memory of the current
+ * device, is misaligned, or whose span runs past the end of its allocation,
+ * found on the host before anything is launched; a missing bound), PT_ECUDA,
+ * PT_ETIMEOUT. */
 #define PT_NOALLOC_MAX_CANDIDATES 4096
 PT_API int pt_objective_noalloc(const void* samples, int64_t n, int dtype, double scale, double fs, double t0,
                                 double smax, const double* cands, int64_t ncand, double* sse_out, int tier,
                                 void* stream);
+
+/* ---- Pipe rates of this GPU (the objective's roofline denominators) --------
+ * The paper has no counterpart: it reports times, not pipe rates. The
+ * objective issues one SFU cosine per sample-evaluation beside a few FP32
+ * FMA-pipe instructions, and the DE's trial generation runs on the FP64 pipe;
+ * these microbenchmarks measure those pipes on the device in use, with one
+ * CTA of 1024 threads per SM running independent chains:
+ *   PT_PIPE_COS   __cosf back to back, each with `nffma` (0, 2, 4, 6 or 8)
+ *                 further FP32 FMAs on other registers;
+ *   PT_PIPE_FFMA  FP32 FMAs alone (nffma ignored);
+ *   PT_PIPE_DFMA  FP64 FMAs alone (nffma ignored);
+ *   PT_PIPE_EX2   ex2.approx back to back, another SFU function, for
+ *                 comparison with the cosine (nffma ignored).
+ * Outputs (host pointers): *per_clk_sm = operations (cosines, or FMAs) per SM
+ * clock per SM, from clock64 counts between CTA barriers (median over SMs);
+ * *per_s = operations per second over the whole GPU (CUDA events);
+ * *sm_mhz = the SM clock those two imply. Best of five launches after one
+ * untimed launch; the call is synchronous on the legacy default stream, makes
+ * `device` current, and allocates and frees a few KB of device memory.
+ * Errors: PT_EINVAL (kind, nffma, device, null outputs), PT_ECUDA. */
+#define PT_PIPE_COS 0
+#define PT_PIPE_FFMA 1
+#define PT_PIPE_DFMA 2
+#define PT_PIPE_EX2 3
+PT_API int pt_pipe_rate(int device, int kind, int nffma, double* per_clk_sm, double* per_s, double* sm_mhz);
 
 /* Device time in milliseconds of the last pt_objective / pt_de_solve kernel
  * work, measured with CUDA events on the context's stream. */
@@ -558,6 +594,15 @@ PT_API int pt_set_wait_timeout(pt_ctx* ctx, double seconds);
  * exchange wait runs out after the wait limit (PT_ETIMEOUT). No fault, trap
  * or unbounded wait is involved. Errors: PT_EINVAL. */
 PT_API int pt_inject_missing_cta(pt_ctx* ctx, int enable);
+
+/* Failure injection for the test of the sample-staging wait, host side: while
+ * enabled, the context's objective and DE launches tell each CTA's staging
+ * mbarrier to expect 16 bytes more than its bulk copies bring (no extra copy,
+ * no other address), so that wait cannot complete and runs out after the wait
+ * limit; the CTA then accounts for the 16 bytes itself, waits (bounded) for
+ * the copies that did run, and returns, and the call reports PT_ETIMEOUT.
+ * The context stays usable. Errors: PT_EINVAL. */
+PT_API int pt_inject_short_tx(pt_ctx* ctx, int enable);
 
 #ifdef __cplusplus
 }

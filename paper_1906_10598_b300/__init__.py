@@ -97,6 +97,8 @@ def load_library():
     lib.pt_set_wait_timeout.restype = c_int
     lib.pt_inject_missing_cta.argtypes = [vp, c_int]
     lib.pt_inject_missing_cta.restype = c_int
+    lib.pt_inject_short_tx.argtypes = [vp, c_int]
+    lib.pt_inject_short_tx.restype = c_int
     _lib = lib
     return lib
 
@@ -252,6 +254,12 @@ class Context:
         """pt_inject_missing_cta: DE launches start one CTA fewer than their
         group (tests of the bounded waits; calls then fail with PT_ETIMEOUT)."""
         self._check(self._lib.pt_inject_missing_cta(self._h, int(bool(enable))))
+
+    def inject_short_tx(self, enable: bool):
+        """pt_inject_short_tx: each CTA's sample-staging wait expects 16 bytes
+        more than its copies bring (test of that wait's limit; calls then fail
+        with PT_ETIMEOUT)."""
+        self._check(self._lib.pt_inject_short_tx(self._h, int(bool(enable))))
 
     def seed_bounds(self, f0_rel: float = 0.1, piece_len: int = 0) -> dict:
         """pt_seed_bounds: the FFT seed of the loaded block's ranges (Sec. 3.1.1);
@@ -436,6 +444,27 @@ def _dvec(a, n):
     v = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
     assert v.size == n
     return v
+
+
+PIPE_COS, PIPE_FFMA, PIPE_DFMA, PIPE_EX2 = 0, 1, 2, 3
+
+
+def pipe_rate(device: int, kind: int, nffma: int = 0) -> dict:
+    """pt_pipe_rate: a pipe microbenchmark on ``device`` (PIPE_COS with
+    ``nffma`` FP32 FMAs per cosine, PIPE_FFMA, PIPE_DFMA, PIPE_EX2). Returns operations
+    per SM clock per SM (clock64), per second over the GPU (CUDA events), and
+    the SM clock in MHz those imply."""
+    lib = load_library()
+    if not hasattr(lib, "_pipe_proto"):
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.pt_pipe_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        lib.pt_pipe_rate.restype = ctypes.c_int
+        lib._pipe_proto = True
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib.pt_pipe_rate(int(device), int(kind), int(nffma), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if rc != PT_OK:
+        raise PhaseTrackError(rc, "pt_pipe_rate failed")
+    return {"per_clk_sm": a.value, "per_s": b.value, "sm_mhz": c.value}
 
 
 def warm_bounds(prev, dt: float, T_next: float, min_f0: float = 0.0, min_f1: float = 0.0, min_f2: float = 0.0):

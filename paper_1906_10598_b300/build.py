@@ -9,7 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libphasetrack.so")
-SOURCES = ["pt_api.cu", "pt_batch.cu", "pt_serve.cu", "pt_noalloc.cu", "pt_track.cu", "pt_seed.cu"]
+SOURCES = ["pt_api.cu", "pt_batch.cu", "pt_serve.cu", "pt_noalloc.cu", "pt_track.cu", "pt_seed.cu",
+           "pt_pipes.cu"]
 DEPS = SOURCES + ["pt_kernels.cuh", "pt_device.cuh", "pt_internal.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-shared",

@@ -15,6 +15,7 @@
 #include "pt_internal.h"
 #include "pt_kernels.cuh"
 
+static_assert(pt::HOST_DE_GROUP_MAX == pt::DE_GROUP_MAX, "host mirror of the DE group limit");
 static_assert(pt::HOST_NP_MAX == pt::NP_MAX && pt::HOST_RING_STRIDE == pt::RING_STRIDE && pt::HOST_L == pt::L &&
                   pt::HOST_D == pt::D && pt::HOST_DMAX == pt::DF && pt::HOST_MODEL_CUBIC == pt::MODEL_CUBIC &&
                   pt::HOST_MODEL_FULL == pt::MODEL_FULL,
@@ -106,6 +107,7 @@ int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
   a.acc = c->d_acc;
   a.err = c->d_err;
   a.timeout_ns = c->timeout_ns;
+  a.extra_tx = c->inject_short_tx ? 16u : 0u;
   const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, a.b.esize, 0, NT, MODEL);
   if (S.total > c->smem_optin) return fail(c, PT_EINVAL, "objective launch needs too much shared memory");
   PT_CUDA(c, cudaFuncSetAttribute(k_objective<TIER, CGV, OBJ, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -259,6 +261,8 @@ namespace pt {
 int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blocks, int nblocks, const int* sched,
                      const int* off, int ngroups, int k, void* d_desc_buf, unsigned long long* ring, int* d_err,
                      int mode, int model) {
+  // the arrival count of a ring word is its low byte (de_block): k <= 255
+  if (k < 1 || k > HOST_DE_GROUP_MAX) return fail(c, PT_EINVAL, "DE group size must be 1 .. 255 CTAs");
   std::vector<DeBlockDesc> desc(nblocks);
   int esize_max = 1;
   int64_t want = 1;
@@ -306,6 +310,7 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   a.ring = ring;
   a.err = d_err;
   a.timeout_ns = c->timeout_ns;
+  a.extra_tx = c->inject_short_tx ? 16u : 0u;
   if (!(mode & DE_LAUNCH)) return PT_OK;
   PT_CUDA(c, cudaMemsetAsync(ring, 0, (size_t)ngroups * RING_GROUP_WORDS * sizeof(unsigned long long), s));
   PT_CUDA(c, cudaMemsetAsync(d_err, 0, sizeof(int), s));
@@ -436,6 +441,12 @@ int pt_inject_missing_cta(pt_ctx* c, int enable) {
   return PT_OK;
 }
 
+int pt_inject_short_tx(pt_ctx* c, int enable) {
+  if (!c) return PT_EINVAL;
+  c->inject_short_tx = enable != 0;
+  return PT_OK;
+}
+
 int pt_set_objective(pt_ctx* c, int objective) {
   if (!c) return PT_EINVAL;
   if (objective != PT_OBJ_CHI2 && objective != PT_OBJ_COR) return fail(c, PT_EINVAL, "unknown objective");
@@ -534,7 +545,7 @@ int de_solve_impl(pt_ctx* c, const double* bounds, int pop, int gens, double F, 
   h.pop_out = c->d_pop;
   h.fit_out = c->d_fit;
   const int sched[1] = {0}, off[2] = {0, 1};
-  const int k = (int)std::min<int64_t>(c->blk.ntiles, c->sms);
+  const int k = (int)std::min<int64_t>(std::min<int64_t>(c->blk.ntiles, c->sms), HOST_DE_GROUP_MAX);
   PT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   rc = launch_de_groups(c, c->stream, tier, &h, 1, sched, off, 1, k, c->d_desc, c->d_ring, c->d_err,
                         DE_UPLOAD | DE_LAUNCH, model);

@@ -87,7 +87,9 @@ double cta_samples(int64_t ntiles, int k) { return (double)((ntiles + k - 1) / k
 // item share spans at most one tile more than ntiles / k).
 bool resident(const pt_ctx* c, int64_t ntiles, int k) { return (ntiles + k - 1) / k + 1 <= c->tune_res_tiles; }
 
-int clamp_k(const pt_ctx* c, int64_t k) { return (int)std::max<int64_t>(1, std::min<int64_t>(k, c->sms)); }
+int clamp_k(const pt_ctx* c, int64_t k) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(k, std::min(c->sms, HOST_DE_GROUP_MAX)));
+}
 
 // Calibrate R_res, R_stream and c_gen (cached in the context for the model
 // they were measured on).
@@ -277,7 +279,7 @@ int create_batch(pt_ctx* c, const pt_block_spec* specs, const double* ext_bounds
   // launch shape
   if ((rc = calibrate(c, tier, b->blocks[0], model)) != PT_OK) return bail(rc);
   std::vector<int> ks;
-  if (group_ctas > 0) ks.push_back(std::min(group_ctas, c->sms));
+  if (group_ctas > 0) ks.push_back(clamp_k(c, group_ctas));
   else
     for (int k : {1, 2, 4, 8, 16, 37, 74, 148})
       if (k <= c->sms) ks.push_back(k);

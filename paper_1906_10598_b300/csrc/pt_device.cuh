@@ -38,6 +38,8 @@ constexpr int NP_MAX = 128;      // largest population / candidate batch per CTA
 // Each candidate's word of the DE exchange ring sits on its own 128-byte line,
 // so the arrivals and polls of different candidates go to different L2 lines.
 constexpr int RING_STRIDE = 16;
+// A ring word's low byte counts the group's arrivals: at most 255 CTAs per group.
+constexpr int DE_GROUP_MAX = 255;
 
 constexpr double TWO_PI = 2.0 * 3.14159265358979323846;
 constexpr double INV_TWO_PI = 0.15915494309189533577;
@@ -544,10 +546,30 @@ __device__ __forceinline__ T warp_reduce_scatter(const T (&v)[N], int lane) {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Bounded wait for phase 0 of `mbar`; true if it completed.
+__device__ __forceinline__ bool mbar_wait_phase0(uint64_t* mbar, uint64_t timeout_ns) {
+  const uint64_t t_start = globaltimer_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(mbar))
+        : "memory");
+    if (done) return true;
+    if (globaltimer_ns() - t_start > timeout_ns) return false;
+  }
+}
+
 // All threads call. Copies `bytes` (multiple of 16, both addresses 16-byte
 // aligned) from `src` to `dst`. Returns false if the bounded wait expired.
+// extra_tx (0 in normal use) is added to the byte count the mbarrier expects
+// without any copy to supply it, so the wait cannot complete and runs out:
+// the test of this wait's limit. The missing bytes are then signalled by the
+// thread itself and the copies that did run are waited for (bounded again),
+// so none is still in flight when the CTA returns.
 __device__ __forceinline__ bool bulk_stage(void* dst, const void* src, uint32_t bytes, uint64_t* mbar,
-                                           uint64_t timeout_ns) {
+                                           uint64_t timeout_ns, uint32_t extra_tx = 0) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
@@ -556,7 +578,8 @@ __device__ __forceinline__ bool bulk_stage(void* dst, const void* src, uint32_t 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                 "r"(bytes + extra_tx)
                  : "memory");
     const uint32_t CHUNK = 32768;
     for (uint32_t off = 0; off < bytes; off += CHUNK) {
@@ -567,24 +590,16 @@ __device__ __forceinline__ bool bulk_stage(void* dst, const void* src, uint32_t 
           "l"((const char*)src + off), "r"(sz), "r"(smem_u32(mbar))
           : "memory");
     }
-    // bounded wait for phase 0
-    const uint64_t t_start = globaltimer_ns();
-    int ok = 0;
-    while (true) {
-      uint32_t done;
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-          : "=r"(done)
-          : "r"(smem_u32(mbar))
-          : "memory");
-      if (done) {
-        ok = 1;
-        // the phase completed: invalidate so the next staging can re-initialise it
-        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
-        break;
-      }
-      if (globaltimer_ns() - t_start > timeout_ns) break;
+    const int ok = mbar_wait_phase0(mbar, timeout_ns) ? 1 : 0;
+    bool complete = ok != 0;
+    if (!ok && extra_tx) {
+      // the injected shortfall: account for it, then wait for the real copies
+      asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(extra_tx)
+                   : "memory");
+      complete = mbar_wait_phase0(mbar, timeout_ns);
     }
+    // once the phase completed, invalidate so the next staging can re-initialise it
+    if (complete) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(mbar)) : "memory");
     s_ok = ok;
   }
   __syncthreads();

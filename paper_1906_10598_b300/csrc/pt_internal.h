@@ -25,6 +25,10 @@ constexpr int HOST_DMAX = 7;     // parameters per candidate of the full model
 constexpr int HOST_MODEL_CUBIC = 0, HOST_MODEL_FULL = 1;
 constexpr int HOST_NP_MAX = 128;
 constexpr int HOST_RING_STRIDE = 16;  // 64-bit words per candidate slot of the DE exchange ring
+// Largest DE group (CTAs solving one block together): each exchange word
+// counts the group's arrivals in its low byte (k_de's ring, pt_kernels.cuh),
+// so a group of 256 or more CTAs would carry into the sum.
+constexpr int HOST_DE_GROUP_MAX = 255;
 // words of one group's DE exchange ring: 3 generations x HOST_NP_MAX candidates
 constexpr size_t RING_GROUP_WORDS = (size_t)3 * HOST_NP_MAX * HOST_RING_STRIDE;
 
@@ -87,6 +91,7 @@ struct pt_ctx {
   float last_ms = 0.f;
   uint64_t timeout_ns = 2000000000ull;
   bool inject_missing_cta = false;  // pt_inject_missing_cta (tests of the bounded waits)
+  bool inject_short_tx = false;     // pt_inject_short_tx (test of the staging wait's limit)
   int objective = 0;  // PT_OBJ_CHI2 or PT_OBJ_COR, for pt_objective and the DE entry points
   int strategy = 0;   // PT_DE_*, for the DE entry points
   // autotune cache of the batched launcher: per-CTA rate and per-generation costs

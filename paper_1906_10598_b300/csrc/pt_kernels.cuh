@@ -669,12 +669,13 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
 
 // Stage tiles [tb, tb + nt) of the block into shared memory and convert them.
 // Returns false (and sets *err) if the bulk copy did not complete in time.
+// extra_tx: see bulk_stage (0 except in the test of the wait's limit).
 template <int TIER>
 __device__ bool stage_tiles(const BlockArgs& b, int64_t tb, int nt, void* raw, float* s32, double* s64,
-                            uint64_t* mbar, uint64_t timeout_ns, int* err) {
+                            uint64_t* mbar, uint64_t timeout_ns, int* err, uint32_t extra_tx = 0) {
   const uint32_t bytes = (uint32_t)nt * (uint32_t)L * (uint32_t)b.esize;
   const char* src = reinterpret_cast<const char*>(b.samples) + tb * (int64_t)L * b.esize;
-  if (!bulk_stage(raw, src, bytes, mbar, timeout_ns)) {
+  if (!bulk_stage(raw, src, bytes, mbar, timeout_ns, extra_tx)) {
     if (threadIdx.x == 0) atomicExch(err, DEV_TIMEOUT);
     return false;
   }
@@ -749,6 +750,7 @@ struct ObjArgs {
   unsigned long long* acc;  // [ncand], zeroed by the caller
   int* err;
   uint64_t timeout_ns;
+  uint32_t extra_tx;        // 0, or the bytes a test of the staging wait adds (bulk_stage)
 };
 
 template <int TIER, int CGV, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
@@ -776,7 +778,7 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   if (tid < npad) acc[tid] = 0ull;
   prep_all<TIER, OBJ, MODEL>(a.cands + (int64_t)cb * model_dim(MODEL), nc, npad, a.b, cdata, negA, kexp, cub,
                              OBJ == OBJ_COR ? COR_BITS_OBJ : SSE_BITS_OBJ);
-  if (!stage_tiles<TIER>(a.b, tb, nt, raw, s32, s64, mbar, a.timeout_ns, a.err)) return;
+  if (!stage_tiles<TIER>(a.b, tb, nt, raw, s32, s64, mbar, a.timeout_ns, a.err, a.extra_tx)) return;
   eval_range<TIER, CGV, OBJ, MODEL>(a.b, tb, 0, nt * (npad / CGV), s32, s64, cdata, negA, kexp, cub, nc, npad, anc,
                                     acc);
   if (tid < nc) atomicAdd(&a.acc[cb + tid], acc[tid]);
@@ -827,6 +829,7 @@ struct DeLaunch {
   int* err;                  // zeroed by the caller
   uint64_t timeout_ns;
   int obj;                   // OBJ_CHI2 or OBJ_COR (the kernel instantiation launched)
+  uint32_t extra_tx;         // 0, or the bytes a test of the staging wait adds (bulk_stage)
 };
 
 struct DeSmem {
@@ -896,7 +899,8 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
   const int ilo = (int)(it0 - tb * G), ihi = (int)(it1 - tb * G);
   const bool resident = nt <= a.sc_tiles;
   const unsigned long long arrived = (unsigned long long)(k & 0xff);
-  if (resident && nt > 0 && !stage_tiles<TIER>(b, tb, nt, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err))
+  if (resident && nt > 0 &&
+      !stage_tiles<TIER>(b, tb, nt, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err, a.extra_tx))
     return false;
 
   for (int gen = 0; gen <= d.gens; ++gen, ++gg) {
@@ -929,7 +933,8 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
       for (int c0 = 0; c0 < nt; c0 += a.sc_tiles) {
         const int cn = min(a.sc_tiles, nt - c0);
         const int lo = max(ilo, c0 * G) - c0 * G, hi = min(ihi, (c0 + cn) * G) - c0 * G;
-        if (!stage_tiles<TIER>(b, tb + c0, cn, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err)) return false;
+        if (!stage_tiles<TIER>(b, tb + c0, cn, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err, a.extra_tx))
+          return false;
         eval_range<TIER, CGV, OBJ, MODEL>(b, tb + c0, lo, hi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub,
                                           np, npad, sm.anc, sm.acc);
       }

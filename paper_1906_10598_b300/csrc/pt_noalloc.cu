@@ -10,9 +10,11 @@
 // device buffers for every input and output, and the only scratch is a
 // file-scope device array of fixed size that every GPU loading the library
 // holds until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <mutex>
 
@@ -50,13 +52,49 @@ int scratch_address(int dev, unsigned long long** out) {
   return PT_OK;
 }
 
-bool on_device(const void* p) {
+// The driver's allocation-range query, looked up once through the runtime (so
+// the library does not link the driver library itself). It only reads the
+// driver's records of existing allocations and allocates nothing.
+typedef CUresult (*AddressRangeFn)(CUdeviceptr* base, size_t* size, CUdeviceptr p);
+AddressRangeFn g_address_range = nullptr;
+bool g_address_range_looked_up = false;
+
+AddressRangeFn address_range_fn() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_address_range_looked_up) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_address_range = reinterpret_cast<AddressRangeFn>(fn);
+    else
+      cudaGetLastError();
+    g_address_range_looked_up = true;
+  }
+  return g_address_range;
+}
+
+// A caller buffer the kernels may use: device (or managed) memory of device
+// `dev`, aligned to `align` bytes, with `bytes` bytes from `p` inside one
+// allocation. The kernels read or write exactly that span; a pointer of
+// another GPU, an unaligned one or a span past the allocation's end would be
+// an invalid access on the device, so each is refused here, before any launch.
+bool usable_buffer(const void* p, int dev, size_t align, size_t bytes) {
   cudaPointerAttributes at;
   if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
+  if (at.type == cudaMemoryTypeDevice && at.device != dev) return false;
+  if (((uintptr_t)p & (align - 1)) != 0) return false;
+  const AddressRangeFn range = address_range_fn();
+  if (!range) return false;
+  CUdeviceptr base = 0;
+  size_t size = 0;
+  if (range(&base, &size, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS) return false;
+  const uintptr_t a = (uintptr_t)p, end = (uintptr_t)base + size;
+  return a >= (uintptr_t)base && a <= end && bytes <= end - a;
 }
 
 template <int TIER, int CGV>
@@ -118,9 +156,14 @@ extern "C" int pt_objective_noalloc(const void* samples, int64_t n, int dtype, d
     smax = bound * scale;
   }
   if (!std::isfinite(smax)) return PT_EINVAL;
-  if (!on_device(samples) || !on_device(cands) || !on_device(sse_out)) return PT_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PT_ECUDA;
+  // the staging copies whole 256-sample tiles with 16-byte-aligned bulk copies
+  const size_t sample_bytes = (size_t)((n + L - 1) / L) * L * (size_t)esize;
+  if (!usable_buffer(samples, dev, 16, sample_bytes) ||
+      !usable_buffer(cands, dev, alignof(double), (size_t)ncand * D * sizeof(double)) ||
+      !usable_buffer(sse_out, dev, alignof(double), (size_t)ncand * sizeof(double)))
+    return PT_EINVAL;
   unsigned long long* scratch = nullptr;
   int rc = scratch_address(dev, &scratch);
   if (rc != PT_OK) return rc;

@@ -137,7 +137,8 @@ int admit(pt_serve_state* S, Slot& sl, Pending& p) {
   h.block_id = b.block_id;
   h.out = sl.d_out;
   const int sched[1] = {0}, off[2] = {0, 1};
-  const int k = (int)std::max<int64_t>(1, std::min<int64_t>(h.blk.ntiles, S->ctas));
+  const int k = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(h.blk.ntiles, S->ctas),
+                                                             HOST_DE_GROUP_MAX));
   rc = launch_de_groups(w, sl.stream, p.req.tier, &h, 1, sched, off, 1, k, sl.d_desc, sl.d_ring, sl.d_err,
                         DE_UPLOAD | DE_LAUNCH, full ? HOST_MODEL_FULL : HOST_MODEL_CUBIC);
   if (rc != PT_OK) return rc;
