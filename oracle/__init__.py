@@ -13,6 +13,8 @@ builds it with gcc and exposes numpy-friendly wrappers:
 * ``sse_full``, ``de_solve_full`` -- the full model of Eq. 2-2-2 (amplitude
   slope c5) with the phase to order n = 4 (Sec. 3.2), 7 parameters.
 * ``de_textbook``         -- the same DE on sphere / Rosenbrock (self-check).
+* ``de_trials``, ``pick3`` -- one generation's trial vectors and draws, and the
+  index draw from given words (pins of the DE's one-step rules).
 * ``philox4x32_10``       -- Salmon et al. SC'11 counter-based generator.
 * ``theta_to_c``, ``c_phase``, ``c_freq``, ``c_total_phase`` -- Eq. 3-1-1 and
   Eq. 4-1-2 observables in the paper's c0..c3 coefficients.
@@ -123,6 +125,13 @@ def _load():
                                                         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, dp, dp, dp,
                                                         ctypes.c_int]
         lib.oc_de_solve_block_full_strategy.restype = ctypes.c_int
+        lib.oc_pick3.argtypes = [ctypes.c_uint32, ctypes.c_uint32, u32p, u32p]
+        lib.oc_pick3.restype = None
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oc_de_trials.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                     dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, u32p, u32p,
+                                     u32p, ip, ip]
+        lib.oc_de_trials.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -223,6 +232,43 @@ def de_solve(samples, fs: float, t0: float, bounds, pop: int, gens: int, F: floa
     if return_population:
         return out[:D].copy(), float(out[D]), popv, fit
     return out[:D].copy(), float(out[D])
+
+
+def pick3(i: int, np_: int, words) -> np.ndarray:
+    """The DE's index draw for individual i of a population of np_ from three
+    given 32-bit words: r1, r2, r3 distinct and different from i."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32))
+    r = np.zeros(3, dtype=np.uint32)
+    p = ctypes.POINTER(ctypes.c_uint32)
+    _load().oc_pick3(ctypes.c_uint32(int(i)), ctypes.c_uint32(int(np_)), w.ctypes.data_as(p), r.ctypes.data_as(p))
+    return r
+
+
+def de_trials(seed: int, block_id: int, gen: int, x, fx, bounds, F: float, CR: float,
+              strategy: str = "rand1bin") -> dict:
+    """One generation's trials (gen >= 1) from population x (pop x dim) with
+    fitness fx: the trial vectors u, the drawn indices r (pop x 3), jrand, the
+    crossover masks take (bit j: component j from the mutant), the either-or
+    coin three_point and the previous generation's best index."""
+    xx = _f64(x)
+    pop, dim = xx.shape
+    f = _f64(fx).reshape(pop)
+    b = _f64(bounds).reshape(dim, 2)
+    u = np.zeros((pop, dim), dtype=np.float64)
+    r = np.zeros((pop, 3), dtype=np.uint32)
+    jr = np.zeros(pop, dtype=np.uint32)
+    tk = np.zeros(pop, dtype=np.uint32)
+    tp = np.zeros(pop, dtype=np.int32)
+    best = ctypes.c_int(-1)
+    up = ctypes.POINTER(ctypes.c_uint32)
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = _load().oc_de_trials(ctypes.c_uint64(int(seed)), ctypes.c_uint32(int(block_id)), ctypes.c_uint32(int(gen)),
+                              int(pop), int(dim), _dptr(xx), _dptr(f), _dptr(b), float(F), float(CR),
+                              int(STRATEGIES[strategy]), _dptr(u), r.ctypes.data_as(up), jr.ctypes.data_as(up),
+                              tk.ctypes.data_as(up), tp.ctypes.data_as(ip), ctypes.byref(best))
+    if rc != 0:
+        raise ValueError("oracle de_trials: invalid arguments")
+    return {"u": u, "r": r, "jrand": jr, "take": tk, "three_point": tp.astype(bool), "best": best.value}
 
 
 def de_textbook(which: str, bounds, pop: int, gens: int, F: float, CR: float, seed: int,

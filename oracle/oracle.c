@@ -229,8 +229,9 @@ static double oc_repair(int j, double u, double parent, const double* lo, const 
 
 /* Three distinct indices different from i, drawn without rejection: the
  * first from NP-1 slots, the second from NP-2, the third from NP-3, each
- * mapped onto the remaining indices in ascending order. */
-static void oc_pick3(uint32_t i, uint32_t np, const uint32_t w[3], uint32_t r[3]) {
+ * mapped onto the remaining indices in ascending order. Exported so the test
+ * suite can feed it chosen words. */
+void oc_pick3(uint32_t i, uint32_t np, const uint32_t w[3], uint32_t r[3]) {
   uint32_t excl[4];
   uint32_t nex = 1;
   excl[0] = i;
@@ -290,6 +291,82 @@ int oc_de_run_dim(oc_objective_fn obj, void* user, int dim, const double* bounds
                   double CR, uint64_t seed, uint32_t block_id, int strategy, double* out, double* final_pop,
                   double* final_fit, int nthreads);
 
+/* The trials of generation g >= 1 (Sec. 1.2: mutation, then crossover), from
+ * the population x (np x dim) of generation g-1 and its fitness fx, with the
+ * bound repair. For each individual i: three indices r from oc_pick3 on
+ * words 0..2 of its counter group draw, jrand = Lemire(word 3, dim), the
+ * crossover mask (component j comes from the mutant when j = jrand, CR >= 1
+ * or word 4+j < floor(CR 2^32)), the strategy's mutant, and the repair of
+ * every component taken from the mutant. Optional outputs (NULL to skip):
+ * r_out (np x 3), jrand_out (np), take_out (np, bit j = component j from the
+ * mutant), three_point_out (np, the either-or strategy's coin), best_out (the
+ * previous generation's lowest-index minimum, used by DE/best/1). */
+static void oc_generation_trials(uint64_t seed, uint32_t block_id, uint32_t g, int np, int dim, const double* x,
+                                 const double* fx, const double* lo, const double* hi, double F, double CR,
+                                 int strategy, double* u, uint32_t* r_out, uint32_t* jrand_out, uint32_t* take_out,
+                                 int* three_point_out, int* best_out) {
+  uint32_t cr_thr = CR >= 1.0 ? 0xffffffffu : (uint32_t)(CR * 4294967296.0);
+  int cr_all = CR >= 1.0;
+  const double K = (F + 1.0) * 0.5;
+  /* the previous generation's best (lowest index on ties), for best/1 */
+  int best = 0;
+  for (int i = 1; i < np; ++i)
+    if (fx[i] < fx[best]) best = i;
+  if (best_out) *best_out = best;
+  for (int i = 0; i < np; ++i) {
+    uint32_t w[12], r[3], w4[4];
+    oc_draw12(seed, block_id, g, (uint32_t)i, w);
+    oc_pick3((uint32_t)i, (uint32_t)np, w, r);
+    uint32_t jrand = oc_lemire(w[3], (uint32_t)dim);
+    if (strategy == OC_DE_BEST1_JITTER) oc_draw_extra(seed, block_id, g, (uint32_t)i, w4);
+    const int three_point = strategy == OC_DE_EITHER_OR && w[9] >= 0x80000000u;
+    uint32_t mask = 0;
+    for (int j = 0; j < dim; ++j) {
+      double parent = x[i * dim + j];
+      const double a = x[r[0] * dim + j], b = x[r[1] * dim + j], c = x[r[2] * dim + j];
+      double v;
+      int take;
+      if (strategy == OC_DE_BEST1_JITTER) {
+        const uint32_t jw = j < 3 ? w[9 + j] : w4[j - 3];
+        const double Fj = F + 1e-4 * ((double)jw * (1.0 / 4294967296.0));
+        v = x[best * dim + j] + Fj * (b - c);
+        take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
+      } else if (strategy == OC_DE_EITHER_OR) {
+        v = three_point ? a + K * ((b + c) - 2.0 * a) : a + F * (b - c);
+        take = 1;
+      } else {
+        v = a + F * (b - c);
+        take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
+      }
+      u[i * dim + j] = take ? oc_repair(j, v, parent, lo, hi) : parent;
+      if (take) mask |= 1u << j;
+    }
+    if (r_out) { r_out[3 * i] = r[0]; r_out[3 * i + 1] = r[1]; r_out[3 * i + 2] = r[2]; }
+    if (jrand_out) jrand_out[i] = jrand;
+    if (take_out) take_out[i] = mask;
+    if (three_point_out) three_point_out[i] = three_point;
+  }
+}
+
+/* Exported form of one generation's trials for the test suite (the DE loop
+ * below calls the same function). bounds: dim (lo, hi) pairs. Returns 0, or
+ * -1 on invalid arguments. */
+int oc_de_trials(uint64_t seed, uint32_t block_id, uint32_t gen, int np, int dim, const double* x, const double* fx,
+                 const double* bounds, double F, double CR, int strategy, double* u, uint32_t* r_out,
+                 uint32_t* jrand_out, uint32_t* take_out, int* three_point_out, int* best_out) {
+  if (np < 4 || gen < 1 || (dim != OC_D && dim != OC_DF)) return -1;
+  if (strategy != OC_DE_RAND1_BIN && strategy != OC_DE_BEST1_JITTER && strategy != OC_DE_EITHER_OR) return -1;
+  double lo[OC_DF], hi[OC_DF];
+  for (int j = 0; j < dim; ++j) {
+    lo[j] = bounds[2 * j];
+    hi[j] = bounds[2 * j + 1];
+    if (!(lo[j] <= hi[j])) return -1;
+  }
+  oc_generation_trials(seed, block_id, gen, np, dim, x, fx, lo, hi, F, CR, strategy, u, r_out, jrand_out, take_out,
+                       three_point_out, best_out);
+  return 0;
+}
+
 int oc_de_run_strategy(oc_objective_fn obj, void* user, const double bounds[2 * OC_D], int np, int gens, double F,
                        double CR, uint64_t seed, uint32_t block_id, int strategy, double out[OC_D + 1],
                        double* final_pop, double* final_fit, int nthreads) {
@@ -346,42 +423,10 @@ int oc_de_run_dim(oc_objective_fn obj, void* user, int dim, const double* bounds
 #endif
   for (int i = 0; i < np; ++i) fx[i] = obj(x + i * dim, user);
 
-  uint32_t cr_thr = CR >= 1.0 ? 0xffffffffu : (uint32_t)(CR * 4294967296.0);
-  int cr_all = CR >= 1.0;
-  const double K = (F + 1.0) * 0.5;
   for (int g = 1; g <= gens; ++g) {
-    /* the previous generation's best (lowest index on ties), for best/1 */
-    int best = 0;
-    for (int i = 1; i < np; ++i)
-      if (fx[i] < fx[best]) best = i;
     /* mutation + crossover for every individual, from the generation-(g-1) population */
-    for (int i = 0; i < np; ++i) {
-      uint32_t w[12], r[3], w4[4];
-      oc_draw12(seed, block_id, (uint32_t)g, (uint32_t)i, w);
-      oc_pick3((uint32_t)i, (uint32_t)np, w, r);
-      uint32_t jrand = oc_lemire(w[3], (uint32_t)dim);
-      if (strategy == OC_DE_BEST1_JITTER) oc_draw_extra(seed, block_id, (uint32_t)g, (uint32_t)i, w4);
-      const int three_point = strategy == OC_DE_EITHER_OR && w[9] >= 0x80000000u;
-      for (int j = 0; j < dim; ++j) {
-        double parent = x[i * dim + j];
-        const double a = x[r[0] * dim + j], b = x[r[1] * dim + j], c = x[r[2] * dim + j];
-        double v;
-        int take;
-        if (strategy == OC_DE_BEST1_JITTER) {
-          const uint32_t jw = j < 3 ? w[9 + j] : w4[j - 3];
-          const double Fj = F + 1e-4 * ((double)jw * (1.0 / 4294967296.0));
-          v = x[best * dim + j] + Fj * (b - c);
-          take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
-        } else if (strategy == OC_DE_EITHER_OR) {
-          v = three_point ? a + K * ((b + c) - 2.0 * a) : a + F * (b - c);
-          take = 1;
-        } else {
-          v = a + F * (b - c);
-          take = (uint32_t)j == jrand || cr_all || w[4 + j] < cr_thr;
-        }
-        u[i * dim + j] = take ? oc_repair(j, v, parent, lo, hi) : parent;
-      }
-    }
+    oc_generation_trials(seed, block_id, (uint32_t)g, np, dim, x, fx, lo, hi, F, CR, strategy, u, NULL, NULL, NULL,
+                         NULL, NULL);
     /* evaluate all trials, then select (trial wins ties) */
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
