@@ -476,6 +476,8 @@ typedef struct pt_track_result {
   double total_phase;      /* phi(T/2) - phi(-T/2) (rad), the Eq. 4-1-2 term; NaN if abandoned */
   double int_doppler;      /* Phi_total / T_c (rad/s) when this block completes a count interval, else NaN */
   double interval_phase;   /* Phi_total of that interval (rad), else NaN */
+  double bounds[14];       /* (lo, hi) pairs of the last search's ranges: A, phi0, f0, f1, f2[, A1, f3]
+                              (the last 4 entries are 0 in a cubic-model session) */
 } pt_track_result;
 
 /* Start a session on ctx (which it uses for every fit; one session per

@@ -596,7 +596,8 @@ class TrackResult(ctypes.Structure):
                 ("params", ctypes.c_double * 7), ("sse", ctypes.c_double), ("dphi", ctypes.c_double),
                 ("dfreq", ctypes.c_double), ("phi_left", ctypes.c_double), ("phi_right", ctypes.c_double),
                 ("f_left", ctypes.c_double), ("f_right", ctypes.c_double), ("total_phase", ctypes.c_double),
-                ("int_doppler", ctypes.c_double), ("interval_phase", ctypes.c_double)]
+                ("int_doppler", ctypes.c_double), ("interval_phase", ctypes.c_double),
+                ("bounds", ctypes.c_double * 14)]
 
 
 def _track_protos(lib):
@@ -649,6 +650,7 @@ class Tracker:
                                                   float(fs), ctypes.byref(r)))
         out = {k: getattr(r, k) for k, _ in TrackResult._fields_}
         out["params"] = np.array(list(r.params)[:self._dim])
+        out["bounds"] = np.array(list(r.bounds)[:2 * self._dim]).reshape(self._dim, 2)
         return out
 
     def close(self):

@@ -180,6 +180,7 @@ int pt_track_block(pt_track* t, const void* samples, int64_t n, int dtype, doubl
   r.f_right = freq_at(p, 0.5 * T);
   r.int_doppler = NaN;
   r.interval_phase = NaN;
+  std::memcpy(r.bounds, b, sizeof(double) * 2 * t->dim);
   if (quality > 0) {
     // Eq. 4-1-2 term: the odd part of the phase across the block (the even
     // f1 and f3 terms cancel between the borders)

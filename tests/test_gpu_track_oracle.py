@@ -1,0 +1,174 @@
+"""Parity of the GPU tracking session (pt_track, Sec. 3.1.4) with the
+oracle's restatement (oracle/track.py), block by block, on three streams: a
+clean stream, a stream with a block of noise (abandoned after three
+searches), and a chirp-rate jump (recovered by the enlarged second search).
+
+* Step by step: the oracle's rules applied to the GPU's own previous fits
+  give the ranges of the GPU's last search (running-time ranges, widened per
+  retry) within 1e-12 relative, the same acceptance decision on the GPU's
+  fit, its continuity residuals, border observables and count-interval
+  phases to rounding.
+* End to end: the oracle's session with its own DE fits (the same Philox
+  keys and block ids) takes the same decisions (quality and searches per
+  block), and its accepted fits agree with the GPU's within the fit
+  tolerances (phi0 1e-3 rad, f0 1e-5 Hz), its integration Doppler within the
+  f0 tolerance's share (2 pi 1e-5 rad/s plus the f2 term).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import track
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1906_10598_b300 as pt
+    from paper_1906_10598_b300 import build
+    build.build()
+    c = pt.Context(0)
+    yield c
+    c.close()
+
+
+def _stream():
+    sp = synth.make_streams(seed=2)[0]  # 10 kHz
+    sp.block_s = 1.0
+    sp.snr_db = 25.0
+    return sp
+
+
+def _kinked_blocks(fs=2000.0, T=1.0, f0=100.0, f1b=8.0, A=1.0, sigma=0.05, seed=0):
+    """Two contiguous blocks of a tone whose chirp rate jumps from 0 to f1b at
+    their shared border (phase and frequency continuous there)."""
+    n = int(round(T * fs))
+    rng = np.random.default_rng(seed)
+    t = np.arange(2 * n) / fs
+    tb = n / fs - 0.5 / fs
+    cyc = f0 * t + np.where(t > tb, f1b * (t - tb) ** 2 / 2, 0.0) + 0.1
+    x = A * np.cos(2 * np.pi * cyc) + rng.normal(0.0, sigma, 2 * n)
+    return x[:n], x[n:]
+
+
+def _cases():
+    sp = _stream()
+    clean = [synth.stream_block(sp, k) for k in range(6)]
+    b0 = clean[0]
+    noise = np.random.default_rng(7).normal(0.0, 1.0, clean[1].n)
+    x0, x1 = _kinked_blocks()
+    return {
+        "clean": dict(bounds=b0.bounds, blocks=[(b.samples, b.fs, b.scale) for b in clean],
+                      cfg=dict(pop=32, gens=800, seed=1, max_dphi=0.3, max_dfreq=2 * math.pi,
+                               count_interval=3 * b0.T)),
+        "noise": dict(bounds=b0.bounds,
+                      blocks=[(clean[0].samples, b0.fs, b0.scale), (noise, b0.fs, 1.0),
+                              (clean[2].samples, b0.fs, b0.scale), (clean[3].samples, b0.fs, b0.scale)],
+                      cfg=dict(pop=32, gens=300, seed=3, max_dphi=0.05, max_dfreq=2 * math.pi * 0.2,
+                               max_attempts=3, count_interval=2 * b0.T)),
+        "chirp_jump": dict(bounds=np.array([[0.8, 1.2], [-np.pi, np.pi], [99.0, 101.0], [-0.5, 0.5], [-0.2, 0.2]]),
+                           blocks=[(x0, 2000.0, 1.0), (x1, 2000.0, 1.0)],
+                           cfg=dict(pop=64, gens=600, seed=5, max_dphi=0.3, max_dfreq=2 * math.pi, enlarge=3.0,
+                                    max_attempts=3)),
+    }
+
+
+def _run_gpu(ctx, case):
+    import paper_1906_10598_b300 as pt
+    tr = pt.Tracker(ctx, case["bounds"], **case["cfg"])
+    try:
+        return [tr.block(s, fs, scale) for s, fs, scale in case["blocks"]]
+    finally:
+        tr.close()
+
+
+CFG_DEFAULTS = dict(enlarge=2.0, max_attempts=3, count_interval=0.0)
+
+
+@pytest.fixture(scope="module")
+def runs(ctx):
+    out = {}
+    for name, case in _cases().items():
+        out[name] = (case, _run_gpu(ctx, case))
+    return out
+
+
+@pytest.mark.parametrize("name", ["clean", "noise", "chirp_jump"])
+def test_gpu_session_follows_the_oracle_rules_step_by_step(runs, name):
+    case, res = runs[name]
+    cfg = dict(CFG_DEFAULTS, **case["cfg"])
+    init = np.asarray(case["bounds"], dtype=np.float64).reshape(-1, 2)
+    dim = init.shape[0]
+    ref, ref_T, gap, adjacent = None, 0.0, 0.0, False
+    acc_phase, acc_T = 0.0, 0.0
+    for k, ((s, fs, scale), r) in enumerate(zip(case["blocks"], res)):
+        T = len(s) / fs
+        assert r["block_index"] == k
+        first = init.copy() if ref is None else track.hold_fixed(
+            track.running_ranges(ref, ref_T / 2 + gap + T / 2, T, dim), init)
+        want = first
+        for _ in range(r["attempts"] - 1):
+            want = track.hold_fixed(track.widen(want, cfg["enlarge"]), init)
+        assert np.allclose(r["bounds"], want, rtol=1e-12, atol=1e-300), (name, k, r["bounds"], want)
+        p = r["params"]
+        if adjacent:
+            dphi, dfreq = track.continuity(ref, ref_T, p, T)
+            assert abs(dphi - r["dphi"]) < 1e-9 and abs(dfreq - r["dfreq"]) <= 1e-9 * max(1.0, abs(dfreq))
+            ok = dphi <= cfg["max_dphi"] and dfreq <= cfg["max_dfreq"]
+            assert ok == (r["quality"] > 0), (name, k)
+            assert r["quality"] in (0, r["attempts"])
+            if not ok:
+                assert r["attempts"] == cfg["max_attempts"]
+        else:
+            assert r["quality"] == 1 and r["attempts"] == 1 and math.isnan(r["dphi"])
+        for key, t in (("phi_left", -T / 2), ("phi_right", T / 2)):
+            assert abs(math.remainder(r[key] - track.phase_rad(p, t), 2 * math.pi)) < 1e-9
+        assert r["f_left"] == pytest.approx(track.freq_rad(p, -T / 2), rel=1e-12, abs=1e-9)
+        assert r["f_right"] == pytest.approx(track.freq_rad(p, T / 2), rel=1e-12, abs=1e-9)
+        if r["quality"]:
+            tp = track.total_phase(p, T)
+            assert r["total_phase"] == pytest.approx(tp, rel=1e-12, abs=1e-9)
+            ref, ref_T, gap, adjacent = p, T, 0.0, True
+            if cfg["count_interval"] > 0:
+                acc_phase += tp
+                acc_T += T
+                if acc_T >= cfg["count_interval"] * (1 - 1e-12):
+                    assert r["interval_phase"] == pytest.approx(acc_phase, rel=1e-12)
+                    assert r["int_doppler"] == pytest.approx(acc_phase / acc_T, rel=1e-12)
+                    acc_phase, acc_T = 0.0, 0.0
+                else:
+                    assert math.isnan(r["int_doppler"])
+        else:
+            assert math.isnan(r["total_phase"]) and math.isnan(r["int_doppler"])
+            adjacent = False
+            if ref is not None:
+                gap += T
+            acc_phase, acc_T = 0.0, 0.0
+
+
+@pytest.mark.parametrize("name", ["clean", "noise", "chirp_jump"])
+def test_gpu_session_matches_the_oracle_session(runs, name):
+    case, res = runs[name]
+    sess = track.TrackSession(case["bounds"], **case["cfg"])
+    worst = 0.0  # the largest Eq. 4-1-2 term difference the fits allow, per second
+    for k, ((s, fs, scale), r) in enumerate(zip(case["blocks"], res)):
+        o = sess.block(np.asarray(s, dtype=np.float64) * scale, fs)
+        assert (o["quality"], o["attempts"]) == (r["quality"], r["attempts"]), (name, k)
+        if o["quality"]:
+            d = abs(math.remainder(o["params"][1] - r["params"][1], 2 * math.pi))
+            assert d <= 1e-3, (name, k, d)
+            assert abs(o["params"][2] - r["params"][2]) <= 1e-5, (name, k, o["params"][2] - r["params"][2])
+            T = len(s) / fs
+            worst = max(worst, 2 * math.pi * (abs(o["params"][2] - r["params"][2])
+                                              + abs(o["params"][4] - r["params"][4]) * T * T / 24))
+        if not math.isnan(o["int_doppler"]):
+            # the interval's phase per second differs by at most the blocks' largest term difference
+            assert abs(o["int_doppler"] - r["int_doppler"]) <= worst * 1.001 + 1e-9, (name, k)
+        else:
+            assert math.isnan(r["int_doppler"])
+    expect = {"clean": None, "noise": [1, 0, 1, 1], "chirp_jump": [1, 2]}[name]
+    if expect:
+        assert [r["quality"] for r in res] == expect
