@@ -39,8 +39,10 @@ METRIC = "objective sample-evals/s"
 UNIT = "sample-evals/s"
 # paper: 400K-sample block, ~80,000 objective evaluations, 6.5 s on a GTX580 (Sec. 1.3)
 PAPER_SAMPLE_EVALS_PER_S = 400_000 * 80_000 / 6.5
-# SFU-bound roofline: 148 SMs x 16 cosine ops/clk/SM x 2032 MHz, one cosine per sample-eval
-SMS, SFU_PER_CLK, SM_MAX_MHZ = 148, 16, 2032.0
+# SFU-bound roofline: one cosine per sample-eval at the pure __cosf rate that
+# pt_pipe_rate measures on this GPU (per SM clock), times the SMs and the
+# maximum SM clock the fits run at (no throttle reason: checked by the clocks)
+SM_MAX_MHZ = 2032.0
 # ncu summary of the DE kernel: its DRAM bytes per launch and the sources it was taken on
 PROFILE = os.path.join(ROOT, "profiles", "k_de_paper400k_full.md")
 PROFILE_FULL_MODEL = os.path.join(ROOT, "profiles", "k_de_perigee400k_full_model.md")
@@ -85,7 +87,7 @@ def _profile_fields(path: str):
     with open(path) as fh:
         for line in fh:
             if ":" in line and line.startswith(("traffic_bytes_per_launch", "kernel_sources_sha256",
-                                                "fp64_pipe_pct_of_peak")):
+                                                "fp64_pipe_pct_of_peak", "warp_inst_per_32_evals")):
                 k, v = line.split(":", 1)
                 fields[k.strip()] = v.strip().strip("`")
     return fields
@@ -102,6 +104,19 @@ def profiled_traffic(path: str = PROFILE):
             os.path.basename(path) + ")"
     except (OSError, KeyError, ValueError):
         return None, "no ncu summary"
+
+
+def profiled_inst_per_32(path: str = PROFILE):
+    """Warp instructions per warp of 32 sample-evaluations of the DE kernel
+    (ncu, all opcodes) from the committed summary, or None once the kernel
+    sources changed since."""
+    try:
+        fields = _profile_fields(path)
+        if fields.get("kernel_sources_sha256") != kernel_sources_sha256():
+            return None
+        return float(fields["warp_inst_per_32_evals"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def profiled_fp64_share(path: str = PROFILE):
@@ -130,6 +145,29 @@ def measure_pipes(device: int, full: bool = True) -> dict:
         out["dfma"] = pt.pipe_rate(device, pt.PIPE_DFMA)
         out["ex2"] = pt.pipe_rate(device, pt.PIPE_EX2)
     return out
+
+
+def sfu_peak(rates: dict) -> dict:
+    """The objective's roofline denominator from the measured pipe rates: one
+    SFU cosine per sample-evaluation at the pure __cosf rate (per SM clock,
+    clock64), times the SM count and the maximum SM clock."""
+    sms = _sm_count()
+    per_clk = rates["cos"]["per_clk_sm"]
+    return {"peak": per_clk * sms * SM_MAX_MHZ * 1e6, "per_clk_sm": per_clk,
+            "measured_per_s": rates["cos"]["per_s"], "measured_mhz": rates["cos"]["sm_mhz"],
+            "basis": f"measured pure __cosf rate {per_clk:.2f}/clk/SM (pt_pipe_rate) x {sms} SMs x "
+                     f"{SM_MAX_MHZ:.0f} MHz, one cosine per sample-eval"}
+
+
+def issue_peak(rates: dict, inst_per_32) -> dict:
+    """The issue-rate ceiling of the kernel: the measured warp instructions per
+    SM clock (FFMA alone) over the kernel's warp instructions per warp of 32
+    sample-evaluations (ncu, all opcodes), or None without a current capture."""
+    if not inst_per_32:
+        return None
+    ipc = rates["ffma"]["per_clk_sm"] / 32.0
+    return {"peak": ipc * 32.0 / inst_per_32 * _sm_count() * SM_MAX_MHZ * 1e6, "warp_inst_per_clk_sm": ipc,
+            "warp_inst_per_32_evals": inst_per_32}
 
 
 def run_peaks(args):
@@ -298,6 +336,8 @@ def run_gpu(args):
     torch.cuda.set_stream(stream)
     ctx.set_stream(stream.cuda_stream)
     ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    # the roofline's denominators, measured on this GPU before the timed region
+    rates = measure_pipes(local, full=False)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2
     bounds = blk.bounds.copy()
     if args.objective == "cor":
@@ -351,15 +391,24 @@ def run_gpu(args):
     value = evals * args.steps * world / (total_ms * 1e-3)
     k_avg = float(np.mean(kern_ms)) * 1e-3
     achieved = evals / k_avg
-    peak = SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6
-    traffic, traffic_note = profiled_traffic(PROFILE_FULL_MODEL if full else PROFILE)
+    sfu = sfu_peak(rates)
+    peak = sfu["peak"]
+    prof = PROFILE_FULL_MODEL if full else PROFILE
+    traffic, traffic_note = profiled_traffic(prof)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
             "traffic": traffic, "traffic_note": traffic_note,
             "kernel": "k_de<TIER_F64, OBJ_CHI2, MODEL_FULL>" if full else "k_de<TIER_F64>",
-            "peak_basis": "148 SMs x 16 SFU cosines/clk x 2032 MHz (one cosine per sample-eval)"}
+            "peak_basis": sfu["basis"], "peak_measured_per_s": sfu["measured_per_s"],
+            "cos_per_clk_sm_measured": sfu["per_clk_sm"]}
     if clocks.get("sm_mhz"):
-        roof["frac_at_measured_clock"] = achieved / (SMS * SFU_PER_CLK * clocks["sm_mhz"] * 1e6)
-    roof["fp64_pipe_share"] = profiled_fp64_share(PROFILE_FULL_MODEL if full else PROFILE)
+        roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+    ip = issue_peak(rates, profiled_inst_per_32(prof))
+    roof["issue_peak"] = ip["peak"] if ip else None
+    roof["frac_of_issue_peak"] = achieved / ip["peak"] if ip else None
+    roof["issue_peak_basis"] = (f"measured {ip['warp_inst_per_clk_sm']:.2f} warp instructions/clk/SM (FFMA alone) / "
+                                f"{ip['warp_inst_per_32_evals']:.2f} warp instructions per 32 sample-evals (ncu)"
+                                if ip else "no ncu capture of the current kernel sources")
+    roof["fp64_pipe_share"] = profiled_fp64_share(prof)
     roof["fp64_pipe_note"] = "ncu sm__inst_executed_pipe_fp64 % of peak over one launch (trial generation, set-up)"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -377,43 +426,73 @@ def run_gpu(args):
                     "d2h_bytes_per_step": (len(params) + 1) * 8 + 8}}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(blk, full=full) if world == 1 else None
+    if world == 1 and not args.no_extras and not full:
+        # the other metrics the workload names, on the same GPU in the same run:
+        # the batched form (256 uneven blocks, one launch under a CUDA graph),
+        # the all-FP64 single-block form on a sample of its blocks, and the
+        # serving loop's latency (4 station streams, compressed replay)
+        ctx.close()
+        ctx = None
+        torch.cuda.set_stream(torch.cuda.default_stream())
+        mb = measure_batch(256, steps=1, warmup=1, e2e_steps=1)
+        ms_ = measure_serve(args.serve_seconds, args.speedup, args.inflight)
+        line["batch_blocks_per_s"] = mb["blocks_per_s"]
+        line["plain_f64_blocks_per_s"] = mb["plain_blocks_per_s"]
+        line["batch_over_plain_f64"] = mb["blocks_per_s"] / mb["plain_blocks_per_s"]
+        line["batch_sample_evals_per_s"] = mb["evals"] / mb["mean_s"]
+        line["batch_frac_of_sfu_peak"] = mb["evals"] / mb["mean_s"] / peak
+        line["batch_fit_sse_rel_err_vs_oracle_max"] = float(max(mb["rel"]))
+        line["serve_p50_ms"] = float(np.percentile(ms_["lat"], 50) * 1e3)
+        line["serve_p99_ms"] = float(np.percentile(ms_["lat"], 99) * 1e3)
+        line["serve_p99_over_block_duration"] = float(np.percentile(ms_["lat_rel"], 99))
+        line["serve_p99_over_real_block_duration"] = float(np.percentile(ms_["lat_real_rel"], 99))
+        line["serve_blocks"] = ms_["n"]
+        line["serve_status_ok"] = ms_["status_ok"]
+        line["extras_config"] = {
+            "batch": "256 blocks, N log-uniform 50K-1M int16, fs 1-50 kHz, pop 32-128, G = ceil(80000/pop); "
+                     "one timed run after one warm-up, CUDA events, L2 flushed",
+            "plain_f64": "all-FP64 tier, one pt_de_solve per block on the batch's quartile- and median-length "
+                         "blocks, blocks/s extrapolated to the batch's sample-evals",
+            "serve": f"4 streams (10/20/35/50 kHz, 1-10 s blocks), {args.serve_seconds:.0f} simulated s replayed "
+                     f"{args.speedup:.0f}x faster than real time, pop 64, 1250 generations, warm-started; "
+                     "latency from arrival to result; serve_p99_over_block_duration is against the compressed "
+                     "duration"}
     if rank == 0:
         line["fit"] = {"params": [float(v) for v in params], "sse": float(sse), "truth": [float(v) for v in blk.truth]}
         print(json.dumps(line))
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-def run_batch(args):
+def measure_batch(nblocks: int, steps: int, warmup: int, full: bool = False, e2e_steps: int = 1,
+                  check_fits: bool = True) -> dict:
     """256 independent blocks of uneven length (N log-uniform 50K-1M int16, fs 1-50
     kHz, pop 32-128, G = ceil(80000/pop)) in one persistent launch under a CUDA
-    graph, launch shape chosen by the autotuner. Compared with the all-FP64
-    single-block form on a sample of the same blocks. With --model full: the
-    same shapes for the full model (synth.batch_full)."""
+    graph, launch shape chosen by the autotuner, timed with CUDA events over
+    `steps` runs (L2 flushed between them). Compared with the all-FP64
+    single-block form on a sample of the same blocks. With full: the same
+    shapes for the full model (synth.batch_full)."""
     import torch
     import oracle
     import paper_1906_10598_b300 as pt
-    from paper_1906_10598_b300 import build
-    build.build()
-    full = args.model == "full"
-    blocks = synth.batch_full(0, nblocks=args.nblocks) if full else synth.batch(0, nblocks=args.nblocks)
+    blocks = synth.batch_full(0, nblocks=nblocks) if full else synth.batch(0, nblocks=nblocks)
     ctx = pt.Context(0)
     stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
     ctx.set_stream(stream.cuda_stream)
     t = time.perf_counter()
     batch = pt.Batch(ctx, blocks, pt.TIER_F64)
     create_s = time.perf_counter() - t
     info = batch.info()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.run()
     sampler = ClockSampler(0)
     sampler.start()
     ms = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         ms.append(batch.run())
@@ -421,12 +500,13 @@ def run_batch(args):
     params, sse = batch.results()
     mean_s = float(np.mean(ms)) * 1e-3
     evals = info["sample_evals"]
-    # fit check on a few blocks against the oracle objective
     rel = []
-    for i in range(0, len(blocks), max(1, len(blocks) // 4)):
-        b = blocks[i]
-        want = (oracle.sse_full if full else oracle.sse)(b.values(), b.fs, b.t0, params[i])
-        rel.append(abs(sse[i] - want) / want)
+    if check_fits:
+        # fit check on a few blocks against the oracle objective
+        for i in range(0, len(blocks), max(1, len(blocks) // 4)):
+            b = blocks[i]
+            want = (oracle.sse_full if full else oracle.sse)(b.values(), b.fs, b.t0, params[i])
+            rel.append(abs(sse[i] - want) / want)
     # all-FP64 single-block form on a sample of the blocks (one pt_de_solve each)
     order = np.argsort([b.n for b in blocks])
     sample_ids = [int(order[len(order) // 4]), int(order[len(order) // 2])]
@@ -443,7 +523,7 @@ def run_batch(args):
     plain_rate = plain_evals / plain_s
     # end to end: fresh batch every step (H2D of every block's samples, launch, results)
     e2e = []
-    for _ in range(max(1, args.steps // 3)):
+    for _ in range(max(1, e2e_steps)):
         torch.cuda.synchronize()
         t = time.perf_counter()
         bb = pt.Batch(ctx, blocks, pt.TIER_F64)
@@ -451,6 +531,22 @@ def run_batch(args):
         bb.results()
         bb.close()
         e2e.append(time.perf_counter() - t)
+    batch.close()
+    ctx.close()
+    return {"blocks": blocks, "info": info, "create_s": create_s, "mean_s": mean_s, "evals": evals,
+            "clocks": clocks, "rel": rel, "plain_rate": plain_rate, "sample_ids": sample_ids, "fast_s": fast_s,
+            "plain_s": plain_s, "e2e_s": float(np.mean(e2e)),
+            "plain_blocks_per_s": len(blocks) / (evals / plain_rate), "blocks_per_s": len(blocks) / mean_s}
+
+
+def run_batch(args):
+    """The batched workload alone (see measure_batch), one JSON line."""
+    from paper_1906_10598_b300 import build
+    build.build()
+    full = args.model == "full"
+    m = measure_batch(args.nblocks, args.steps, args.warmup, full=full, e2e_steps=max(1, args.steps // 3))
+    blocks, info, evals, mean_s = m["blocks"], m["info"], m["evals"], m["mean_s"]
+    sfu = sfu_peak(measure_pipes(0, full=False))
     nbytes = int(sum(b.samples.nbytes for b in blocks))
     line = {"metric": "batched objective sample-evals/s", "value": evals / mean_s, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
@@ -461,46 +557,43 @@ def run_batch(args):
                        "group_ctas": info["group_ctas"], "groups": info["ngroups"],
                        "uses_graph": info["uses_graph"], "autotune_predicted_ms": info["predicted_ms"],
                        "tune_rate_per_cta": info["tune_rate"], "tune_gen_us": info["tune_gen_us"],
-                       "tune_rate_stream_per_cta": info["tune_rate_stream"], "create_s": create_s},
-            "blocks_per_s": len(blocks) / mean_s,
-            "roofline": {"bound": "alu", "achieved": evals / mean_s, "peak": SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6,
-                         "unit": UNIT, "frac": evals / mean_s / (SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6),
-                         "traffic": None,
-                         "kernel": "k_de<TIER_F64, OBJ_CHI2, MODEL_FULL> (grouped)" if full else "k_de<TIER_F64> (grouped)"},
-            "plain_f64_single_block": {"sample_evals_per_s": plain_rate,
-                                       "blocks_per_s_est": len(blocks) / (evals / plain_rate),
-                                       "sampled_blocks": sample_ids,
-                                       "default_tier_single_block_s": fast_s, "plain_tier_single_block_s": plain_s},
-            "fit_sse_rel_err_vs_oracle_max": float(max(rel)),
-            "clocks": clocks, "gpu_launches": args.steps,
-            "e2e": {"value": evals / float(np.mean(e2e)), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                       "tune_rate_stream_per_cta": info["tune_rate_stream"], "create_s": m["create_s"]},
+            "blocks_per_s": m["blocks_per_s"],
+            "roofline": {"bound": "alu", "achieved": evals / mean_s, "peak": sfu["peak"], "unit": UNIT,
+                         "frac": evals / mean_s / sfu["peak"], "traffic": None, "peak_basis": sfu["basis"],
+                         "kernel": "k_de<TIER_F64, OBJ_CHI2, MODEL_FULL> (grouped)" if full else
+                         "k_de<TIER_F64> (grouped)"},
+            "plain_f64_single_block": {"sample_evals_per_s": m["plain_rate"],
+                                       "blocks_per_s_est": m["plain_blocks_per_s"],
+                                       "sampled_blocks": m["sample_ids"],
+                                       "default_tier_single_block_s": m["fast_s"],
+                                       "plain_tier_single_block_s": m["plain_s"]},
+            "fit_sse_rel_err_vs_oracle_max": float(max(m["rel"])),
+            "clocks": m["clocks"], "gpu_launches": args.steps,
+            "e2e": {"value": evals / m["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": len(blocks) * 64}}
     print(json.dumps(line))
-    batch.close()
-    ctx.close()
     return 0
 
 
-def run_serve(args):
+def measure_serve(sim_seconds: float, speedup: float, inflight: int) -> dict:
     """Four simulated station streams (10/20/35/50 kHz, 1-10 s blocks, drifting
     Doppler) deliver blocks as they fill, in real time compressed by
-    `--speedup`; each block is submitted on arrival (pt_submit), warm-started
+    `speedup`; each block is submitted on arrival (pt_submit), warm-started
     from the stream's latest fit (Sec. 3.1.1 running-time ranges), and
     collected with pt_poll. Latency = completion - arrival."""
     import paper_1906_10598_b300 as pt
-    from paper_1906_10598_b300 import build
-    build.build()
     specs = synth.make_streams(0)
-    X = args.speedup
+    X = speedup
     plan = []  # (arrival_sim_s, stream, index, block)
     for sp in specs:
-        nb = max(2, int(args.sim_seconds // sp.block_s))
+        nb = max(2, int(sim_seconds // sp.block_s))
         for k in range(nb):
             b = synth.stream_block(sp, k)
             plan.append(((k + 1) * sp.block_s, sp.stream_id, k, b))
     plan.sort(key=lambda x: x[0])
     ctx = pt.Context(0)
-    server = pt.Server(ctx, max_inflight=args.inflight, ctas_per_request=0, max_queued=256)
+    server = pt.Server(ctx, max_inflight=inflight, ctas_per_request=0, max_queued=256)
     # warm up the kernels once
     w = plan[0][3]
     ctx.load_block(w.samples, w.fs, w.t0, w.scale)
@@ -555,25 +648,36 @@ def run_serve(args):
             cont += int(ok)
             ncont += 1
     evals = sum(plan[j][3].sample_evals() for j in results)
-    line = {"metric": "served blocks/s", "value": len(results) / wall, "unit": "blocks/s", "n_gpus": 1,
-            "steps": len(results), "warmup": 1, "ms_per_step": wall / len(results) * 1e3, "higher_is_better": True,
+    ctx.close()
+    return {"specs": specs, "X": X, "n": len(results), "wall": wall, "lat": lat, "lat_rel": lat_rel,
+            "lat_real_rel": [v / X for v in lat_rel], "f0err": f0err, "inb": inb, "cont": cont, "ncont": ncont,
+            "evals": evals, "status_ok": sum(r["status"] == 0 for r in results.values()) / len(results)}
+
+
+def run_serve(args):
+    """The serving replay alone (see measure_serve), one JSON line."""
+    from paper_1906_10598_b300 import build
+    build.build()
+    m = measure_serve(args.sim_seconds, args.speedup, args.inflight)
+    specs, lat, lat_rel = m["specs"], m["lat"], m["lat_rel"]
+    line = {"metric": "served blocks/s", "value": m["n"] / m["wall"], "unit": "blocks/s", "n_gpus": 1,
+            "steps": m["n"], "warmup": 1, "ms_per_step": m["wall"] / m["n"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serve4_streams_10-50khz_1-10s", "streams": len(specs),
                        "block_s": [sp.block_s for sp in specs], "fs": [sp.fs for sp in specs],
-                       "time_compression": X, "sim_seconds": args.sim_seconds, "max_inflight": args.inflight,
+                       "time_compression": m["X"], "sim_seconds": args.sim_seconds, "max_inflight": args.inflight,
                        "pop": 64, "gens": 1250},
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                            "max": float(np.max(lat) * 1e3)},
             "latency_over_block_duration": {"p50": float(np.percentile(lat_rel, 50)),
                                             "p99": float(np.percentile(lat_rel, 99)),
                                             "note": "block duration compressed by time_compression"},
-            "sample_evals_per_s": evals / wall,
-            "warm_start_truth_in_bounds": inb / len(results),
-            "continuity_pass": cont / max(1, ncont),
-            "f0_abs_err_hz": {"median": float(np.median(f0err)), "max": float(np.max(f0err))},
-            "status_ok": sum(r["status"] == 0 for r in results.values()) / len(results)}
+            "sample_evals_per_s": m["evals"] / m["wall"],
+            "warm_start_truth_in_bounds": m["inb"] / m["n"],
+            "continuity_pass": m["cont"] / max(1, m["ncont"]),
+            "f0_abs_err_hz": {"median": float(np.median(m["f0err"])), "max": float(np.max(m["f0err"]))},
+            "status_ok": m["status_ok"]}
     print(json.dumps(line))
-    ctx.close()
     return 0
 
 
@@ -616,7 +720,8 @@ def run_objective(args):
     evals = float(blk.n) * args.ncand
     value = evals * args.steps / (float(np.sum(ms)) * 1e-3)
     achieved = evals / (float(np.mean(kms)) * 1e-3)
-    peak = SMS * SFU_PER_CLK * SM_MAX_MHZ * 1e6
+    sfu = sfu_peak(measure_pipes(0, full=False))
+    peak = sfu["peak"]
     got = out.cpu().numpy()
     idx = np.arange(0, args.ncand, max(1, args.ncand // 8))
     import oracle
@@ -627,8 +732,7 @@ def run_objective(args):
             "config": {"workload": "paper400k_int16_objective", "n": blk.n, "candidates": args.ncand,
                        "tier": "f64-anchored phase, f32 cos", "l2": "flushed between steps"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-                         "traffic": None, "kernel": "k_objective<TIER_F64, 16>",
-                         "peak_basis": "148 SMs x 16 SFU cosines/clk x 2032 MHz (one cosine per sample-eval)"},
+                         "traffic": None, "kernel": "k_objective<TIER_F64, 16>", "peak_basis": sfu["basis"]},
             "clocks": clocks, "gpu_launches": 2 * args.steps,
             "sse_rel_err_vs_oracle_max": float(np.max(np.abs(got[idx] - want) / want))}
     print(json.dumps(line))
@@ -884,6 +988,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="single: skip the batch / all-FP64 / serving measurements added to the line")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="single: simulated seconds of the serving replay added to the line")
     ap.add_argument("--mode", default="single",
                     choices=["single", "batch", "serve", "precision", "track", "objective", "seed", "peaks"],
                     help="single: the 400K-block fit (default); batch: 256 uneven blocks in one launch; "

@@ -54,11 +54,14 @@ def test_profile_figures_follow_the_kernel_hash(path, tmp_path):
     fields = bench._profile_fields(path)
     traffic, note = bench.profiled_traffic(path)
     share = bench.profiled_fp64_share(path)
+    inst = bench.profiled_inst_per_32(path)
     if fields.get("kernel_sources_sha256") == bench.kernel_sources_sha256():
         assert traffic == int(fields["traffic_bytes_per_launch"]) and traffic > 0
         assert share == pytest.approx(float(fields["fp64_pipe_pct_of_peak"]) / 100.0)
+        if "warp_inst_per_32_evals" in fields:
+            assert inst == pytest.approx(float(fields["warp_inst_per_32_evals"])) and inst > 0
     else:
-        assert traffic is None and share is None
+        assert traffic is None and share is None and inst is None
     # a summary whose hash does not match gives no figures
     stale = tmp_path / "stale.md"
     stale.write_text(open(path).read().replace(fields["kernel_sources_sha256"], "0" * 64))
