@@ -15,7 +15,8 @@
 #include "pt_internal.h"
 #include "pt_kernels.cuh"
 
-static_assert(pt::HOST_DE_GROUP_MAX == pt::DE_GROUP_MAX, "host mirror of the DE group limit");
+static_assert(pt::HOST_DE_GROUP_MAX == pt::DE_GROUP_MAX && pt::HOST_RING_SLOTS == pt::RING_SLOTS,
+              "host mirrors of the DE group limit and ring depth");
 static_assert(pt::HOST_NP_MAX == pt::NP_MAX && pt::HOST_RING_STRIDE == pt::RING_STRIDE && pt::HOST_L == pt::L &&
                   pt::HOST_D == pt::D && pt::HOST_DMAX == pt::DF && pt::HOST_MODEL_CUBIC == pt::MODEL_CUBIC &&
                   pt::HOST_MODEL_FULL == pt::MODEL_FULL,

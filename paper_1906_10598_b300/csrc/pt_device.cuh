@@ -40,6 +40,9 @@ constexpr int NP_MAX = 128;      // largest population / candidate batch per CTA
 constexpr int RING_STRIDE = 16;
 // A ring word's low byte counts the group's arrivals: at most 255 CTAs per group.
 constexpr int DE_GROUP_MAX = 255;
+// Generations the DE exchange ring holds (see de_block: slot g + 2 is cleared
+// during generation g's wait).
+constexpr int RING_SLOTS = 4;
 
 constexpr double TWO_PI = 2.0 * 3.14159265358979323846;
 constexpr double INV_TWO_PI = 0.15915494309189533577;

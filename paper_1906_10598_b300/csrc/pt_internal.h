@@ -29,8 +29,9 @@ constexpr int HOST_RING_STRIDE = 16;  // 64-bit words per candidate slot of the 
 // counts the group's arrivals in its low byte (k_de's ring, pt_kernels.cuh),
 // so a group of 256 or more CTAs would carry into the sum.
 constexpr int HOST_DE_GROUP_MAX = 255;
-// words of one group's DE exchange ring: 3 generations x HOST_NP_MAX candidates
-constexpr size_t RING_GROUP_WORDS = (size_t)3 * HOST_NP_MAX * HOST_RING_STRIDE;
+// words of one group's DE exchange ring: HOST_RING_SLOTS generations x HOST_NP_MAX candidates
+constexpr int HOST_RING_SLOTS = 4;
+constexpr size_t RING_GROUP_WORDS = (size_t)HOST_RING_SLOTS * HOST_NP_MAX * HOST_RING_STRIDE;
 
 // Per-block constants computed at load time (same meaning as BlockArgs).
 struct HostBlock {

@@ -825,7 +825,7 @@ struct DeLaunch {
   int ngroups, k;
   int sc_tiles;              // tiles staged per CTA at a time (shared-memory budget)
   int esize_max;             // largest sample size in the launch (shared-memory layout)
-  unsigned long long* ring;  // [ngroups][3][NP_MAX][RING_STRIDE], zeroed by the caller
+  unsigned long long* ring;  // [ngroups][RING_SLOTS][NP_MAX][RING_STRIDE], zeroed by the caller
   int* err;                  // zeroed by the caller
   uint64_t timeout_ns;
   int obj;                   // OBJ_CHI2 or OBJ_COR (the kernel instantiation launched)
@@ -875,7 +875,7 @@ __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& s
 // the whole population and generates every trial itself (identical Philox
 // draws, identical FP64 arithmetic), so the only exchange is each trial's SSE:
 // every CTA adds (partial << 8) | 1 to the trial's 64-bit word of the group's
-// 3-deep ring, whose low byte counts arrivals; a word whose low byte equals k
+// RING_SLOTS-deep ring, whose low byte counts arrivals; a word whose low byte equals k
 // holds the complete fixed-point sum, and one acquire load per candidate
 // replaces a barrier, a fence and a separate read. `gg` counts the group's
 // generations across blocks so the ring discipline continues from block to
@@ -904,16 +904,7 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     return false;
 
   for (int gen = 0; gen <= d.gens; ++gen, ++gg) {
-    unsigned long long* slot = ring + (gg % 3) * (NP_MAX * RING_STRIDE);
-    // the ring slot of the group's next generation was last read before the
-    // previous generation ended everywhere: rank 0 clears it, and its fence
-    // orders the clear before its own contributions to this generation, which
-    // every reader acquires before contributing to the next one
-    // (every word of the slot: the group's next block may have a larger population)
-    if (rank == 0 && tid < NP_MAX) {
-      ring[((gg + 1) % 3) * (NP_MAX * RING_STRIDE) + tid * RING_STRIDE] = 0ull;
-      __threadfence();
-    }
+    unsigned long long* slot = ring + (gg % RING_SLOTS) * (NP_MAX * RING_STRIDE);
     // trials u of this generation (the initial population at gen 0)
     if (gen == 0) {
       if (tid < np) de_init<DIM>(d.dc, tid, sm.u + tid * DIM);
@@ -942,13 +933,7 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     if (tid < np) {
       unsigned long long* w = slot + tid * RING_STRIDE;
       const unsigned long long contrib = (sm.acc[tid] << 8) | 1ull;
-      if (rank == 0) {
-        // release: orders rank 0's clear of the next slot (by any of its
-        // threads, before the CTA barrier above) before this contribution
-        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(w), "l"(contrib) : "memory");
-      } else {
-        atomicAdd(w, contrib);
-      }
+      atomicAdd(w, contrib);
       // wait for every CTA's contribution to this candidate, then select
       const uint64_t t_start = globaltimer_ns();
       unsigned long long v;
@@ -979,6 +964,16 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
 #pragma unroll
         for (int j = 0; j < DIM; ++j) sm.x[tid * DIM + j] = sm.u[tid * DIM + j];
       }
+    } else if (rank == 0 && tid >= 2 * NP_MAX && tid < 3 * NP_MAX) {
+      // Slot gg + 2 was last used at generation gg - 2, whose words every CTA
+      // read before contributing to gg - 1, which rank 0 has seen complete;
+      // rank 0 clears it now, off the exchange's critical path, and the fence
+      // puts the clear before the closing barrier, so before rank 0's
+      // contributions to gg + 1, which every CTA observes before it
+      // contributes to gg + 2. (Every word of the slot: the group's next block
+      // may have a larger population.)
+      ring[((gg + 2) % RING_SLOTS) * (NP_MAX * RING_STRIDE) + (tid - 2 * NP_MAX) * RING_STRIDE] = 0ull;
+      __threadfence();
     } else if (gen < d.gens && tid >= NP_MAX && tid < NP_MAX + np) {
       // the next generation's draws do not depend on selection: overlap them with the wait
       const int c = tid - NP_MAX;
@@ -1041,7 +1036,7 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
 
   const int q = blockIdx.x / a.k, rank = blockIdx.x - q * a.k;
   if (q >= a.ngroups) return;
-  unsigned long long* ring = a.ring + (size_t)q * 3 * NP_MAX * RING_STRIDE;
+  unsigned long long* ring = a.ring + (size_t)q * RING_SLOTS * NP_MAX * RING_STRIDE;
   unsigned long long gg = 0;
   __shared__ DeBlockDesc s_desc;
   for (int e = a.sched_off[q]; e < a.sched_off[q + 1]; ++e) {
