@@ -165,22 +165,33 @@ size_t smem_de(int tier, int sc_tiles, int esize_max, int model) {
   return smem_layout(tier, NP_MAX, sc_tiles, 16, esize_max, NP_MAX, NT, model).total;
 }
 
-template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
+template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC, int SK = -1>
 int launch_de_t(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
   const size_t smem = smem_de(TIER, a.sc_tiles, a.esize_max, MODEL);
   cudaFuncAttributes fa{};
-  PT_CUDA(c, cudaFuncGetAttributes(&fa, k_de<TIER, OBJ, MODEL>));
+  PT_CUDA(c, cudaFuncGetAttributes(&fa, k_de<TIER, OBJ, MODEL, SK>));
   if (smem + fa.sharedSizeBytes > c->smem_optin) return fail(c, PT_EINVAL, "DE launch needs too much shared memory");
-  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, OBJ, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, OBJ, MODEL, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, OBJ, MODEL>, NT, smem));
+  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, OBJ, MODEL, SK>, NT, smem));
   // pt_inject_missing_cta: the last group's last rank is not started, so its
   // arrivals never come and the others' bounded waits run out
   const int grid = a.ngroups * a.k - (c->inject_missing_cta && a.ngroups * a.k > 1 ? 1 : 0);
   if (occ < 1 || grid > occ * c->sms) return fail(c, PT_EINVAL, "DE grid cannot be co-resident");
   void* args[] = {&a};
-  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, OBJ, MODEL>, dim3(grid), dim3(NT), args, smem, s));
+  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, OBJ, MODEL, SK>, dim3(grid), dim3(NT), args, smem, s));
   return PT_OK;
+}
+
+// The default tier's DE kernels are compiled per strategy (every block of a
+// launch has the context's strategy).
+template <int OBJ, int MODEL = MODEL_CUBIC>
+int launch_de_f64(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
+  switch (c->strategy) {
+    case DE_BEST1_JITTER: return launch_de_t<TIER_F64, OBJ, MODEL, DE_BEST1_JITTER>(c, s, a);
+    case DE_EITHER_OR: return launch_de_t<TIER_F64, OBJ, MODEL, DE_EITHER_OR>(c, s, a);
+    default: return launch_de_t<TIER_F64, OBJ, MODEL, DE_RAND1_BIN>(c, s, a);
+  }
 }
 
 // Device layout of the descriptor buffer: blocks | sched | sched_off.
@@ -319,7 +330,7 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
     // the full model: the chi-square (checked by the entry points)
     a.obj = OBJ_CHI2;
     switch (tier) {
-      case PT_TIER_F64: return launch_de_t<TIER_F64, OBJ_CHI2, MODEL_FULL>(c, s, a);
+      case PT_TIER_F64: return launch_de_f64<OBJ_CHI2, MODEL_FULL>(c, s, a);
       case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN, OBJ_CHI2, MODEL_FULL>(c, s, a);
       case PT_TIER_DF32: return launch_de_t<TIER_DF32, OBJ_CHI2, MODEL_FULL>(c, s, a);
       default: return launch_de_t<TIER_F32, OBJ_CHI2, MODEL_FULL>(c, s, a);
@@ -328,14 +339,14 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   a.obj = c->objective;
   if (a.obj == OBJ_COR) {
     switch (tier) {
-      case PT_TIER_F64: return launch_de_t<TIER_F64, OBJ_COR>(c, s, a);
+      case PT_TIER_F64: return launch_de_f64<OBJ_COR>(c, s, a);
       case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN, OBJ_COR>(c, s, a);
       case PT_TIER_DF32: return launch_de_t<TIER_DF32, OBJ_COR>(c, s, a);
       default: return launch_de_t<TIER_F32, OBJ_COR>(c, s, a);
     }
   }
   switch (tier) {
-    case PT_TIER_F64: return launch_de_t<TIER_F64>(c, s, a);
+    case PT_TIER_F64: return launch_de_f64<OBJ_CHI2>(c, s, a);
     case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN>(c, s, a);
     case PT_TIER_DF32: return launch_de_t<TIER_DF32>(c, s, a);
     default: return launch_de_t<TIER_F32>(c, s, a);

@@ -14,6 +14,8 @@
 // depend on the launch shape, the CTA count or the order of completion.
 #pragma once
 
+#include <climits>
+
 #include "pt_device.cuh"
 
 namespace pt {
@@ -847,23 +849,42 @@ struct DeSmem {
   void* raw;
 };
 
+// The lowest-index minimum of fx[0 .. np) (the order of dkey), found by a
+// whole warp: each lane takes every 32nd individual in ascending order, then
+// a shuffle reduction keeps the smaller key, or on equal keys the smaller
+// index, so the result is the first minimum a sequential scan would find.
+// Every lane of the warp must call it.
+__device__ __forceinline__ int lowest_minimum_warp(const double* fx, int np, int lane) {
+  long long bk = LLONG_MAX;
+  int bi = INT_MAX;
+  for (int i = lane; i < np; i += 32) {
+    const long long ki = dkey(fx[i]);
+    if (ki < bk) {
+      bk = ki;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ok < bk || (ok == bk && oi < bi)) {
+      bk = ok;
+      bi = oi;
+    }
+  }
+  return bi;
+}
+
 // Every trial component of the generation, one thread per (individual, component).
 // DE_BEST1_JITTER mutates from the previous generation's lowest-index
-// minimum, which each thread finds itself (broadcast reads of the fitnesses,
-// no extra CTA barrier in the generation loop).
+// minimum, which every warp finds itself (lowest_minimum_warp: broadcast
+// reads of the fitnesses, no extra CTA barrier in the generation loop).
+// Called by every thread of the CTA.
 template <int STRAT, int DIM = D>
 __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& sm, int np, int npad) {
   int best = 0;
-  if (STRAT == DE_BEST1_JITTER) {
-    long long bk = dkey(sm.fx[0]);
-    for (int i = 1; i < np; ++i) {
-      const long long ki = dkey(sm.fx[i]);
-      if (ki < bk) {
-        bk = ki;
-        best = i;
-      }
-    }
-  }
+  if (STRAT == DE_BEST1_JITTER) best = lowest_minimum_warp(sm.fx, np, threadIdx.x & 31);
   for (int t = threadIdx.x; t < DIM * npad; t += blockDim.x) {
     const int j = t / npad, c = t - j * npad;
     if (c < np)
@@ -881,10 +902,12 @@ __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& s
 // generations across blocks so the ring discipline continues from block to
 // block. Returns false if a bounded wait expired or another CTA failed.
 // MODEL_FULL: the full model's 7 parameters (chi-square).
-template <int TIER, int CGV, int OBJ, int MODEL = MODEL_CUBIC>
+// SK: the launch's strategy when fixed at compile time, -1 to read it from the block.
+template <int TIER, int CGV, int OBJ, int MODEL = MODEL_CUBIC, int SK = -1>
 __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long long* ring, unsigned long long& gg,
                          const DeSmem& sm, const DeLaunch& a, int* s_abort) {
   constexpr int DIM = model_dim(MODEL);
+  const int strat = SK >= 0 ? SK : d.dc.strategy;
   const int tid = threadIdx.x;
   const int np = d.np, npad = (d.np + CGV - 1) / CGV * CGV;
   const BlockArgs& b = d.b;
@@ -909,8 +932,8 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     if (gen == 0) {
       if (tid < np) de_init<DIM>(d.dc, tid, sm.u + tid * DIM);
     } else {
-      if (d.dc.strategy == DE_BEST1_JITTER) mutate_all<DE_BEST1_JITTER, DIM>(d, sm, np, npad);
-      else if (d.dc.strategy == DE_EITHER_OR) mutate_all<DE_EITHER_OR, DIM>(d, sm, np, npad);
+      if (strat == DE_BEST1_JITTER) mutate_all<DE_BEST1_JITTER, DIM>(d, sm, np, npad);
+      else if (strat == DE_EITHER_OR) mutate_all<DE_EITHER_OR, DIM>(d, sm, np, npad);
       else mutate_all<DE_RAND1_BIN, DIM>(d, sm, np, npad);
     }
     if (tid < npad) sm.acc[tid] = 0ull;
@@ -977,9 +1000,9 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     } else if (gen < d.gens && tid >= NP_MAX && tid < NP_MAX + np) {
       // the next generation's draws do not depend on selection: overlap them with the wait
       const int c = tid - NP_MAX;
-      if (d.dc.strategy == DE_BEST1_JITTER)
+      if (strat == DE_BEST1_JITTER)
         de_draws<DE_BEST1_JITTER, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * DIM);
-      else if (d.dc.strategy == DE_EITHER_OR)
+      else if (strat == DE_EITHER_OR)
         de_draws<DE_EITHER_OR, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * DIM);
       else
         de_draws<DE_RAND1_BIN, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * DIM);
@@ -1007,8 +1030,10 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
 
 // Persistent DE launch over groups of blocks (one block: one group of all CTAs).
 // Launched cooperatively: the k CTAs of a group wait on one another. OBJ
-// selects the objective every block of the launch minimises.
-template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
+// selects the objective every block of the launch minimises; SK, when not -1,
+// the DE strategy of all its blocks (each strategy's kernel then holds only
+// its own trial code).
+template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC, int SK = -1>
 __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int DIM = model_dim(MODEL);
@@ -1045,9 +1070,11 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
     __syncthreads();
     const DeBlockDesc& d = s_desc;
     bool ok;
-    if (TIER == TIER_F64 && d.cg == 16) ok = de_block<TIER, 16, OBJ, MODEL>(d, rank, a.k, ring, gg, sm, a, &s_abort);
-    else if (TIER == TIER_F64 && d.cg == 4) ok = de_block<TIER, 4, OBJ, MODEL>(d, rank, a.k, ring, gg, sm, a, &s_abort);
-    else ok = de_block<TIER, 8, OBJ, MODEL>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    if (TIER == TIER_F64 && d.cg == 16)
+      ok = de_block<TIER, 16, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    else if (TIER == TIER_F64 && d.cg == 4)
+      ok = de_block<TIER, 4, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+    else ok = de_block<TIER, 8, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort);
     if (!ok) return;
   }
 }
