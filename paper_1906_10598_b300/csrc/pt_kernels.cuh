@@ -140,15 +140,20 @@ __device__ __forceinline__ void prep_zero(unsigned char* cdata, float* negA, int
 // The default tier spreads the four FP64 polynomial terms and the amplitude
 // over separate threads so the 1/64-rate FP64 work is spread across all
 // warps of the CTA, and flags in cub[c] the candidates whose cubic term must
-// stay exact (cubic_needed). Ends with __syncthreads().
-// The full model (default tier, chi-square) spreads its five terms and the
-// amplitude/flag/exponent work the same way.
+// stay exact (cubic_needed). The full model (default tier, chi-square)
+// spreads its five terms and the amplitude/flag/exponent work the same way.
+// Tasks are taken from `first` in steps of `stride` (a thread range of the
+// CTA); with a list, only the candidates list[0 .. nlist) (all below nc) are
+// prepared, with one >= 0 only candidate `one`. No barrier.
 template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
-__device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs& b, unsigned char* cdata,
-                         float* negA, int* kexp, unsigned char* cub, int kbits) {
+__device__ void prep_range(const double* cands, int nc, int npad, const BlockArgs& b, unsigned char* cdata,
+                           float* negA, int* kexp, unsigned char* cub, int kbits, int first, int stride,
+                           const unsigned char* list = nullptr, int nlist = 0, int one = -1) {
+  const int m = one >= 0 ? 1 : list ? nlist : npad;
   if constexpr (MODEL == MODEL_FULL && TIER == TIER_F64) {
-    for (int t = threadIdx.x; t < 6 * npad; t += blockDim.x) {
-      const int k = t / npad, c = t - k * npad;
+    for (int t = first; t < 6 * m; t += stride) {
+      const int k = t / m, i = t - k * m;
+      const int c = one >= 0 ? one : list ? (int)list[i] : i;
       const double* th = cands + c * DF;
       unsigned char* cd = cdata + c * CAND_BYTES_FULL;
       if (k < 4) {
@@ -173,8 +178,9 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
       }
     }
   } else if constexpr (TIER == TIER_F64) {
-    for (int t = threadIdx.x; t < 5 * npad; t += blockDim.x) {
-      const int k = t / npad, c = t - k * npad;
+    for (int t = first; t < 5 * m; t += stride) {
+      const int k = t / m, i = t - k * m;
+      const int c = one >= 0 ? one : list ? (int)list[i] : i;
       if (k < 4) {
         const double E = c < nc ? poly_coef(cands + c * D, b, k) : 0.0;
         reinterpret_cast<u128*>(cdata + c * CAND_BYTES)[k] = frac128(E);
@@ -190,13 +196,21 @@ __device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs&
     }
   } else {
     constexpr int CB = cand_bytes(MODEL);
-    for (int c = threadIdx.x; c < npad; c += blockDim.x) {
+    for (int i = first; i < m; i += stride) {
+      const int c = one >= 0 ? one : list ? (int)list[i] : i;
       if (c < nc)
         prep_candidate<TIER, OBJ, MODEL>(cands + c * model_dim(MODEL), b, cdata + c * CB, negA + c, kexp + c, kbits);
       else prep_zero<MODEL>(cdata + c * CB, negA + c, kexp + c);
       cub[c] = 0;
     }
   }
+}
+
+// All of the CTA prepares candidates [0, nc) padded to npad; ends with __syncthreads().
+template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
+__device__ void prep_all(const double* cands, int nc, int npad, const BlockArgs& b, unsigned char* cdata,
+                         float* negA, int* kexp, unsigned char* cub, int kbits) {
+  prep_range<TIER, OBJ, MODEL>(cands, nc, npad, b, cdata, negA, kexp, cub, kbits, threadIdx.x, blockDim.x);
   __syncthreads();
 }
 
@@ -538,11 +552,16 @@ __device__ __forceinline__ bool any_flag(const unsigned char* f) {
 // go to warps round-robin; for
 // the default tier each warp computes the tile anchors of its next IPB items
 // itself into its own slice of `anc` (IPB * CGV entries per warp), so no
-// CTA-wide barrier separates anchors from evaluation. Ends with __syncthreads().
-template <int TIER, int CGV, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
+// CTA-wide barrier separates anchors from evaluation. Each warp then calls
+// hook(warp) (work for warps that finish early); ends with __syncthreads().
+struct NoHook {
+  __device__ void operator()(int) const {}
+};
+template <int TIER, int CGV, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC, class Hook = NoHook>
 __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, int item_hi, const float* s32,
                            const double* s64, const unsigned char* cdata, const float* negA, const int* kexp,
-                           const unsigned char* cub, int ncand, int npad, uint4* anc, unsigned long long* acc) {
+                           const unsigned char* cub, int ncand, int npad, uint4* anc, unsigned long long* acc,
+                           const Hook& hook = Hook()) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int G = npad / CGV;
   const int nitems = item_hi;
@@ -666,6 +685,7 @@ __device__ void eval_range(const BlockArgs& b, int64_t tile_begin, int item_lo, 
     }
     __syncwarp();
   }
+  hook(warp);
   __syncthreads();
 }
 
@@ -694,7 +714,7 @@ __device__ bool stage_tiles(const BlockArgs& b, int64_t tb, int nt, void* raw, f
 // Shared-memory carve-up common to both kernels.
 struct SmemLayout {
   size_t off_mbar, off_cdata, off_negA, off_kexp, off_cub, off_acc, off_draw, off_anc, off_samp, off_raw, off_pop,
-      total;
+      off_u2, off_cdata2, off_negA2, off_kexp2, off_cub2, off_win, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -702,10 +722,14 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 // npad: padded candidates; tmax: max tiles per CTA; cgv: candidates per item;
 // pop: population slots (0 for the objective kernel); nthreads: CTA size.
 // model: MODEL_CUBIC or MODEL_FULL (wider population rows, candidate data and anchors).
+// With pop > 0 (the DE): two generations' draws, and a second set of trials
+// and set-up (the next generation's, built ahead) with a flag per individual;
+// the current generation's set keeps fixed offsets ahead of them.
 __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, int cgv, int esize, int pop,
                                                   int nthreads, int model = MODEL_CUBIC) {
   SmemLayout s;
   size_t o = 0;
+  const size_t ahead = pop ? 1 : 0;
   s.off_mbar = o;
   o += 16;
   s.off_pop = o;
@@ -721,8 +745,20 @@ __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, 
   s.off_acc = o;
   o += align_up((size_t)npad * sizeof(unsigned long long), 16);
   s.off_draw = o;
-  // rpack, take and model_dim jitter words per individual
-  o += align_up((size_t)(pop ? (2 + model_dim(model)) * npad : 0) * sizeof(uint32_t), 16);
+  // rpack, take and model_dim jitter words per individual, for two generations
+  o += align_up((size_t)(pop ? 2 * (2 + model_dim(model)) * npad : 0) * sizeof(uint32_t), 16);
+  s.off_u2 = o;
+  o += ahead * align_up((size_t)pop * model_dim(model) * sizeof(double), 16);
+  s.off_cdata2 = o;
+  o += ahead * (size_t)npad * cand_bytes(model);
+  s.off_negA2 = o;
+  o += ahead * align_up((size_t)npad * sizeof(float), 16);
+  s.off_kexp2 = o;
+  o += ahead * align_up((size_t)npad * sizeof(int), 16);
+  s.off_cub2 = o;
+  o += ahead * align_up((size_t)npad, 16);
+  s.off_win = o;
+  o += ahead * align_up((size_t)npad, 16);
   s.off_anc = o;
   o += (tier == TIER_F64) ? (size_t)(nthreads / 32) * IPB * cgv * anchor_words(model) * sizeof(uint4) : 0;
   s.off_samp = o;
@@ -834,6 +870,12 @@ struct DeLaunch {
   uint32_t extra_tx;         // 0, or the bytes a test of the staging wait adds (bulk_stage)
 };
 
+// One generation's draws: packed indices, crossover mask, model_dim jitter
+// words per individual.
+struct Draws {
+  uint32_t *drp, *drt, *drj;
+};
+
 struct DeSmem {
   uint64_t* mbar;
   double *x, *u, *fx;
@@ -842,7 +884,15 @@ struct DeSmem {
   int* kexp;
   unsigned char* cub;
   unsigned long long* acc;
-  uint32_t *drp, *drt, *drj;  // packed indices, crossover mask, model_dim jitter words per individual
+  // the next generation's trials and set-up, when built ahead (AheadHook)
+  double* u2;
+  unsigned char* cdata2;
+  float* negA2;
+  int* kexp2;
+  unsigned char* cub2;
+  unsigned char* win;   // per individual: replaced at the last selection
+  Draws dr0, dr1;       // generation g's draws are set g & 1 (picked by value, off the evaluation)
+  __device__ __forceinline__ Draws draws(int g) const { return (g & 1) ? dr1 : dr0; }
   uint4* anc;
   float* s32;
   double* s64;
@@ -876,19 +926,142 @@ __device__ __forceinline__ int lowest_minimum_warp(const double* fx, int np, int
   return bi;
 }
 
-// Every trial component of the generation, one thread per (individual, component).
-// DE_BEST1_JITTER mutates from the previous generation's lowest-index
-// minimum, which every warp finds itself (lowest_minimum_warp: broadcast
-// reads of the fitnesses, no extra CTA barrier in the generation loop).
-// Called by every thread of the CTA.
+// Trial components of the generation from population x and draws dr into u:
+// with a list, every component of the trials list[0 .. nlist), otherwise of
+// all np trials; one (individual, component) per thread, from `first` in
+// steps of `stride`. DE_BEST1_JITTER mutates from the previous generation's
+// lowest-index minimum (of fx), which every warp finds itself
+// (lowest_minimum_warp: broadcast reads of the fitnesses, no extra CTA
+// barrier); its callers are whole warps.
 template <int STRAT, int DIM = D>
-__device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& sm, int np, int npad) {
+__device__ __forceinline__ void mutate_all(const DeControls& dc, const double* x, const double* fx, double* u,
+                                           const Draws& dr, int np, int npad, int first, int stride,
+                                           const unsigned char* list = nullptr, int nlist = 0) {
   int best = 0;
-  if (STRAT == DE_BEST1_JITTER) best = lowest_minimum_warp(sm.fx, np, threadIdx.x & 31);
-  for (int t = threadIdx.x; t < DIM * npad; t += blockDim.x) {
-    const int j = t / npad, c = t - j * npad;
+  if (STRAT == DE_BEST1_JITTER) best = lowest_minimum_warp(fx, np, threadIdx.x & 31);
+  const int m = list ? nlist : npad;
+  for (int t = first; t < DIM * m; t += stride) {
+    const int j = t / m, i = t - j * m;
+    const int c = list ? (int)list[i] : i;
     if (c < np)
-      sm.u[c * DIM + j] = de_component<STRAT, DIM>(d.dc, sm.x, c, j, sm.drp[c], sm.drt[c], best, sm.drj + c * DIM);
+      u[c * DIM + j] = de_component<STRAT, DIM>(dc, x, c, j, dr.drp[c], dr.drt[c], best, dr.drj + c * DIM);
+  }
+}
+
+template <int DIM = D>
+__device__ __forceinline__ void mutate_any(int strat, const DeControls& dc, const double* x, const double* fx,
+                                           double* u, const Draws& dr, int np, int npad, int first, int stride,
+                                           const unsigned char* list = nullptr, int nlist = 0) {
+  if (strat == DE_BEST1_JITTER)
+    mutate_all<DE_BEST1_JITTER, DIM>(dc, x, fx, u, dr, np, npad, first, stride, list, nlist);
+  else if (strat == DE_EITHER_OR)
+    mutate_all<DE_EITHER_OR, DIM>(dc, x, fx, u, dr, np, npad, first, stride, list, nlist);
+  else mutate_all<DE_RAND1_BIN, DIM>(dc, x, fx, u, dr, np, npad, first, stride, list, nlist);
+}
+
+// Generation `gen`'s draws for individual c into dr.
+template <int DIM = D>
+__device__ __forceinline__ void draw_any(int strat, const DeControls& dc, int np, int c, uint32_t gen,
+                                         const Draws& dr) {
+  if (strat == DE_BEST1_JITTER)
+    de_draws<DE_BEST1_JITTER, DIM>(dc, np, c, gen, &dr.drp[c], &dr.drt[c], dr.drj + c * DIM);
+  else if (strat == DE_EITHER_OR)
+    de_draws<DE_EITHER_OR, DIM>(dc, np, c, gen, &dr.drp[c], &dr.drt[c], dr.drj + c * DIM);
+  else de_draws<DE_RAND1_BIN, DIM>(dc, np, c, gen, &dr.drp[c], &dr.drt[c], dr.drj + c * DIM);
+}
+
+__device__ __forceinline__ void bar_sync_named(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Warps that hold one item fewer than warp 0 leave the evaluation early; while
+// the others finish, warps first_warp .. end build the next generation's
+// trials (its draws are ready) and their set-up, into the second set, from the
+// current population, as if the coming selection replaced no individual.
+// After the selection the trials that read a replaced individual (their own
+// parent or one of their three donors) are rebuilt; every other trial has
+// exactly the inputs, and so the bits, that the generation would have
+// computed after the selection. Named barrier 1 orders the trials before
+// their set-up among these warps only. Not for DE_BEST1_JITTER, whose base
+// vector is the selection's best.
+template <int DIM, int TIER, int OBJ, int MODEL>
+struct AheadHook {
+  const DeControls* dc;
+  const BlockArgs* b;
+  const DeSmem* sm;
+  Draws dr;
+  int strat, np, npad, first_warp, kbits;
+  __device__ void operator()(int warp) const {
+    if (warp < first_warp) return;
+    const int nthr = (int)blockDim.x - first_warp * 32, q = (int)threadIdx.x - first_warp * 32;
+    if (strat == DE_EITHER_OR)
+      mutate_all<DE_EITHER_OR, DIM>(*dc, sm->x, nullptr, sm->u2, dr, np, npad, q, nthr);
+    else mutate_all<DE_RAND1_BIN, DIM>(*dc, sm->x, nullptr, sm->u2, dr, np, npad, q, nthr);
+    bar_sync_named(1, nthr);
+    prep_range<TIER, OBJ, MODEL>(sm->u2, np, npad, *b, sm->cdata2, sm->negA2, sm->kexp2, sm->cub2, kbits, q, nthr);
+  }
+};
+
+// Fewest early warps worth building the next generation ahead, and most
+// individuals the last selection may have replaced for it (acceptance is high
+// early in a fit, when most trials would be rebuilt anyway; on the 400K block
+// a limit of 1 beat 0, 2, 4, 8 and 16).
+constexpr int AHEAD_MIN_WARPS = 4;
+constexpr int AHEAD_MAX_REPLACED = 1;
+
+// After a selection that replaced individuals, rebuild in the current buffers
+// the trials built ahead that read one of them (their own parent or a
+// donor): every warp finds the stale set itself (a trial and its three donor
+// flags per lane, a ballot per 32 trials), and warp w rebuilds the stale
+// trials of rank w, w + nw, ...: its lanes make the trial's components, then
+// its set-up tasks. No barrier: the caller's next one orders the results.
+template <int DIM, int TIER, int OBJ, int MODEL>
+__device__ __forceinline__ void rebuild_stale(int strat, const DeControls& dc, const BlockArgs& b, const DeSmem& sm,
+                                              const Draws& dr, int np, int npad, int kbits) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int rank = 0;
+  for (int c0 = 0; c0 < np; c0 += 32) {
+    const int c = c0 + lane;
+    bool stale = false;
+    if (c < np) {
+      const uint32_t rp = dr.drp[c];
+      stale = (sm.win[c] | sm.win[rp & 0xff] | sm.win[(rp >> 8) & 0xff] | sm.win[(rp >> 16) & 0xff]) != 0;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, stale);
+    while (m) {
+      const int t = c0 + __ffs(m) - 1;
+      m &= m - 1u;
+      if (rank++ % nw != warp) continue;
+      if (lane < DIM) {
+        sm.u[t * DIM + lane] =
+            strat == DE_EITHER_OR
+                ? de_component<DE_EITHER_OR, DIM>(dc, sm.x, t, lane, dr.drp[t], dr.drt[t], 0, dr.drj + t * DIM)
+                : de_component<DE_RAND1_BIN, DIM>(dc, sm.x, t, lane, dr.drp[t], dr.drt[t], 0, dr.drj + t * DIM);
+      }
+      __syncwarp();
+      prep_range<TIER, OBJ, MODEL>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub, kbits, lane, 32, nullptr,
+                                   0, t);
+      __syncwarp();
+    }
+  }
+}
+
+// During the exchange wait (this generation's evaluation done), threads
+// `first` in steps of `stride` move the set-up built ahead into the current
+// buffers: every candidate's row, -A and flag, and the exponents of the
+// padding candidates; each of the first np candidates' poller moves its
+// exponent and trial row itself once it has used them.
+template <int MODEL>
+__device__ __forceinline__ void take_ahead_setup(const DeSmem& sm, int np, int npad, int first, int stride) {
+  constexpr int CB = cand_bytes(MODEL);
+  static_assert(CB % 16 == 0, "candidate rows copy as 16-byte words");
+  const uint4* src = reinterpret_cast<const uint4*>(sm.cdata2);
+  uint4* dst = reinterpret_cast<uint4*>(sm.cdata);
+  for (int i = first; i < npad * (CB / 16); i += stride) dst[i] = src[i];
+  for (int i = first; i < npad; i += stride) {
+    sm.negA[i] = sm.negA2[i];
+    sm.cub[i] = sm.cub2[i];
+    if (i >= np) sm.kexp[i] = sm.kexp2[i];
   }
 }
 
@@ -900,15 +1073,21 @@ __device__ __forceinline__ void mutate_all(const DeBlockDesc& d, const DeSmem& s
 // holds the complete fixed-point sum, and one acquire load per candidate
 // replaces a barrier, a fence and a separate read. `gg` counts the group's
 // generations across blocks so the ring discipline continues from block to
-// block. Returns false if a bounded wait expired or another CTA failed.
+// block. Generation g's draws are made during generation g - 2's exchange
+// wait; its trials and set-up are built during generation g - 1's evaluation
+// where the CTA has early warps and the last selection replaced few
+// individuals (AheadHook), else after the selection. s_nrep[2] counts each
+// generation's replacements. Returns false if a bounded wait expired or
+// another CTA failed.
 // MODEL_FULL: the full model's 7 parameters (chi-square).
 // SK: the launch's strategy when fixed at compile time, -1 to read it from the block.
 template <int TIER, int CGV, int OBJ, int MODEL = MODEL_CUBIC, int SK = -1>
 __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long long* ring, unsigned long long& gg,
-                         const DeSmem& sm, const DeLaunch& a, int* s_abort) {
+                         const DeSmem& sm, const DeLaunch& a, int* s_abort, int* s_nrep) {
   constexpr int DIM = model_dim(MODEL);
+  constexpr int KBITS = OBJ == OBJ_COR ? COR_BITS_DE : SSE_BITS_DE;
   const int strat = SK >= 0 ? SK : d.dc.strategy;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, nw = (int)(blockDim.x >> 5);
   const int np = d.np, npad = (d.np + CGV - 1) / CGV * CGV;
   const BlockArgs& b = d.b;
   // this CTA's share of the block's items (tile, candidate group), in tile
@@ -922,25 +1101,46 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
   const int ilo = (int)(it0 - tb * G), ihi = (int)(it1 - tb * G);
   const bool resident = nt <= a.sc_tiles;
   const unsigned long long arrived = (unsigned long long)(k & 0xff);
+  // items go to warps round-robin, so warps rem .. nw - 1 hold one item fewer
+  // than warp 0 (none when rem = 0)
+  const int rem = (ihi - ilo) % nw;
+  const int first_early =
+      (resident && strat != DE_BEST1_JITTER && rem > 0 && nw - rem >= AHEAD_MIN_WARPS) ? rem : -1;
   if (resident && nt > 0 &&
       !stage_tiles<TIER>(b, tb, nt, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err, a.extra_tx))
     return false;
 
+  bool ahead = false;  // this generation's trials and set-up were built during the last evaluation
   for (int gen = 0; gen <= d.gens; ++gen, ++gg) {
     unsigned long long* slot = ring + (gg % RING_SLOTS) * (NP_MAX * RING_STRIDE);
-    // trials u of this generation (the initial population at gen 0)
+    const Draws dr = sm.draws(gen);
+    // replacements at the last selection (all of generation 0's)
+    const int nrep = gen > 0 ? s_nrep[(gen - 1) & 1] : np;
+    if (tid == 0) s_nrep[gen & 1] = 0;
+    // trials u of this generation (the initial population at gen 0) and their set-up
     if (gen == 0) {
       if (tid < np) de_init<DIM>(d.dc, tid, sm.u + tid * DIM);
+      if (tid < npad) sm.acc[tid] = 0ull;
+      __syncthreads();
+      prep_all<TIER, OBJ, MODEL>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub, KBITS);
+    } else if (ahead) {
+      // the trials and set-up built ahead are in place (moved during the last
+      // exchange); those that read an individual the selection replaced are rebuilt
+      if (nrep > 0) {
+        rebuild_stale<DIM, TIER, OBJ, MODEL>(strat, d.dc, b, sm, dr, np, npad, KBITS);
+        __syncthreads();
+      }
     } else {
-      if (strat == DE_BEST1_JITTER) mutate_all<DE_BEST1_JITTER, DIM>(d, sm, np, npad);
-      else if (strat == DE_EITHER_OR) mutate_all<DE_EITHER_OR, DIM>(d, sm, np, npad);
-      else mutate_all<DE_RAND1_BIN, DIM>(d, sm, np, npad);
+      mutate_any<DIM>(strat, d.dc, sm.x, sm.fx, sm.u, dr, np, npad, tid, blockDim.x);
+      __syncthreads();
+      prep_all<TIER, OBJ, MODEL>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub, KBITS);
     }
-    if (tid < npad) sm.acc[tid] = 0ull;
-    __syncthreads();
-    prep_all<TIER, OBJ, MODEL>(sm.u, np, npad, b, sm.cdata, sm.negA, sm.kexp, sm.cub,
-                               OBJ == OBJ_COR ? COR_BITS_DE : SSE_BITS_DE);
-    if (resident) {
+    const bool build_next = first_early >= 0 && gen >= 1 && gen < d.gens && nrep <= AHEAD_MAX_REPLACED;
+    if (build_next) {
+      const AheadHook<DIM, TIER, OBJ, MODEL> hook{&d.dc, &b, &sm, sm.draws(gen + 1), strat, np, npad, first_early, KBITS};
+      eval_range<TIER, CGV, OBJ, MODEL>(b, tb, ilo, ihi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
+                                        sm.anc, sm.acc, hook);
+    } else if (resident) {
       eval_range<TIER, CGV, OBJ, MODEL>(b, tb, ilo, ihi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
                                         sm.anc, sm.acc);
     } else {
@@ -949,13 +1149,15 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
         const int lo = max(ilo, c0 * G) - c0 * G, hi = min(ihi, (c0 + cn) * G) - c0 * G;
         if (!stage_tiles<TIER>(b, tb + c0, cn, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err, a.extra_tx))
           return false;
-        eval_range<TIER, CGV, OBJ, MODEL>(b, tb + c0, lo, hi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub,
-                                          np, npad, sm.anc, sm.acc);
+        eval_range<TIER, CGV, OBJ, MODEL>(b, tb + c0, lo, hi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np,
+                                          npad, sm.anc, sm.acc);
       }
     }
+    ahead = build_next;
     if (tid < np) {
       unsigned long long* w = slot + tid * RING_STRIDE;
       const unsigned long long contrib = (sm.acc[tid] << 8) | 1ull;
+      sm.acc[tid] = 0ull;  // for the next generation (the closing barrier orders it)
       atomicAdd(w, contrib);
       // wait for every CTA's contribution to this candidate, then select
       const uint64_t t_start = globaltimer_ns();
@@ -982,10 +1184,19 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
       const double f = OBJ == OBJ_COR
                            ? -(sm.u[tid * DIM] * signed_fixed_to_double((long long)v >> 8, sm.kexp[tid]))
                            : fixed_to_double(v >> 8, sm.kexp[tid]);
-      if (gen == 0 || dkey(f) <= dkey(sm.fx[tid])) {
+      const bool replace = gen == 0 || dkey(f) <= dkey(sm.fx[tid]);
+      if (replace) {
         sm.fx[tid] = f;
 #pragma unroll
         for (int j = 0; j < DIM; ++j) sm.x[tid * DIM + j] = sm.u[tid * DIM + j];
+        atomicAdd(&s_nrep[gen & 1], 1);
+      }
+      sm.win[tid] = replace ? 1 : 0;
+      if (build_next) {
+        // the next generation's trial and exponent, built ahead, now that this one's are used
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) sm.u[tid * DIM + j] = sm.u2[tid * DIM + j];
+        sm.kexp[tid] = sm.kexp2[tid];
       }
     } else if (rank == 0 && tid >= 2 * NP_MAX && tid < 3 * NP_MAX) {
       // Slot gg + 2 was last used at generation gg - 2, whose words every CTA
@@ -997,15 +1208,14 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
       // may have a larger population.)
       ring[((gg + 2) % RING_SLOTS) * (NP_MAX * RING_STRIDE) + (tid - 2 * NP_MAX) * RING_STRIDE] = 0ull;
       __threadfence();
-    } else if (gen < d.gens && tid >= NP_MAX && tid < NP_MAX + np) {
-      // the next generation's draws do not depend on selection: overlap them with the wait
-      const int c = tid - NP_MAX;
-      if (strat == DE_BEST1_JITTER)
-        de_draws<DE_BEST1_JITTER, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * DIM);
-      else if (strat == DE_EITHER_OR)
-        de_draws<DE_EITHER_OR, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * DIM);
-      else
-        de_draws<DE_RAND1_BIN, DIM>(d.dc, np, c, (uint32_t)(gen + 1), &sm.drp[c], &sm.drt[c], sm.drj + c * DIM);
+    } else if (tid >= NP_MAX && tid < NP_MAX + np) {
+      // draws do not depend on selection: generation gen + 2's are made during
+      // this wait, into the set generation gen has finished with
+      if (gen + 2 <= d.gens) draw_any<DIM>(strat, d.dc, np, tid - NP_MAX, (uint32_t)(gen + 2), dr);
+    } else if (gen == 0 && d.gens >= 1 && tid >= 3 * NP_MAX && tid < 3 * NP_MAX + np) {
+      draw_any<DIM>(strat, d.dc, np, tid - 3 * NP_MAX, 1u, sm.dr1);
+    } else if (build_next && tid >= 3 * NP_MAX) {
+      take_ahead_setup<MODEL>(sm, np, npad, tid - 3 * NP_MAX, (int)blockDim.x - 3 * NP_MAX);
     }
     __syncthreads();
     if (*s_abort) return false;
@@ -1048,14 +1258,23 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
   sm.kexp = reinterpret_cast<int*>(smem + S.off_kexp);
   sm.cub = smem + S.off_cub;
   sm.acc = reinterpret_cast<unsigned long long*>(smem + S.off_acc);
-  sm.drp = reinterpret_cast<uint32_t*>(smem + S.off_draw);
-  sm.drt = sm.drp + NP_MAX;
-  sm.drj = sm.drp + 2 * NP_MAX;
+  sm.u2 = reinterpret_cast<double*>(smem + S.off_u2);
+  sm.cdata2 = smem + S.off_cdata2;
+  sm.negA2 = reinterpret_cast<float*>(smem + S.off_negA2);
+  sm.kexp2 = reinterpret_cast<int*>(smem + S.off_kexp2);
+  sm.cub2 = smem + S.off_cub2;
+  sm.win = smem + S.off_win;
+  sm.dr0.drp = reinterpret_cast<uint32_t*>(smem + S.off_draw);
+  sm.dr0.drt = sm.dr0.drp + NP_MAX;
+  sm.dr0.drj = sm.dr0.drp + 2 * NP_MAX;
+  sm.dr1.drp = sm.dr0.drp + (2 + DIM) * NP_MAX;
+  sm.dr1.drt = sm.dr1.drp + NP_MAX;
+  sm.dr1.drj = sm.dr1.drp + 2 * NP_MAX;
   sm.anc = reinterpret_cast<uint4*>(smem + S.off_anc);
   sm.s32 = reinterpret_cast<float*>(smem + S.off_samp);
   sm.s64 = reinterpret_cast<double*>(smem + S.off_samp);
   sm.raw = smem + S.off_raw;
-  __shared__ int s_abort;
+  __shared__ int s_abort, s_nrep[2];
   if (threadIdx.x == 0) s_abort = 0;
   __syncthreads();
 
@@ -1071,10 +1290,10 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
     const DeBlockDesc& d = s_desc;
     bool ok;
     if (TIER == TIER_F64 && d.cg == 16)
-      ok = de_block<TIER, 16, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+      ok = de_block<TIER, 16, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort, s_nrep);
     else if (TIER == TIER_F64 && d.cg == 4)
-      ok = de_block<TIER, 4, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort);
-    else ok = de_block<TIER, 8, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort);
+      ok = de_block<TIER, 4, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort, s_nrep);
+    else ok = de_block<TIER, 8, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort, s_nrep);
     if (!ok) return;
   }
 }
