@@ -161,13 +161,13 @@ int launch_objective_any(pt_ctx* c, int tier, const double* d_cands, int ncand, 
 
 // ---- grouped DE --------------------------------------------------------------
 
-size_t smem_de(int tier, int sc_tiles, int esize_max, int model) {
-  return smem_layout(tier, NP_MAX, sc_tiles, 16, esize_max, NP_MAX, NT, model).total;
+size_t smem_de(int tier, int sc_tiles, int esize_max, int model, bool ahead) {
+  return smem_layout(tier, NP_MAX, sc_tiles, 16, esize_max, NP_MAX, NT, model, ahead).total;
 }
 
 template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC, int SK = -1>
 int launch_de_t(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
-  const size_t smem = smem_de(TIER, a.sc_tiles, a.esize_max, MODEL);
+  const size_t smem = smem_de(TIER, a.sc_tiles, a.esize_max, MODEL, a.ahead != 0);
   cudaFuncAttributes fa{};
   PT_CUDA(c, cudaFuncGetAttributes(&fa, k_de<TIER, OBJ, MODEL, SK>));
   if (smem + fa.sharedSizeBytes > c->smem_optin) return fail(c, PT_EINVAL, "DE launch needs too much shared memory");
@@ -206,9 +206,9 @@ size_t de_desc_bytes(int nblocks, int ngroups) { return o_off(nblocks) + (size_t
 // under 1 KB) comes out of the same per-block opt-in budget as the dynamic part.
 constexpr size_t DE_STATIC_SMEM_RESERVE = 2048;
 
-int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want, int model) {
+int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want, int model, bool ahead) {
   int sc = (int)std::max<int64_t>(1, std::min<int64_t>(want, 96));
-  while (sc > 1 && smem_de(tier, sc, esize_max, model) + DE_STATIC_SMEM_RESERVE > c->smem_optin) sc--;
+  while (sc > 1 && smem_de(tier, sc, esize_max, model, ahead) + DE_STATIC_SMEM_RESERVE > c->smem_optin) sc--;
   return sc;
 }
 
@@ -317,7 +317,12 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   a.sched_off = (const int*)(base + o_off(nblocks));
   a.ngroups = ngroups;
   a.k = k;
-  a.sc_tiles = pick_sc_tiles(c, tier, esize_max, want, model);
+  // the next generation is built ahead only on resident tiles, so its second
+  // trial set is laid out only when every block's share fits beside it; else
+  // the staging chunk gets that shared memory
+  a.sc_tiles = pick_sc_tiles(c, tier, esize_max, want, model, true);
+  a.ahead = a.sc_tiles >= want ? 1 : 0;
+  if (!a.ahead) a.sc_tiles = pick_sc_tiles(c, tier, esize_max, want, model, false);
   a.esize_max = esize_max;
   a.ring = ring;
   a.err = d_err;

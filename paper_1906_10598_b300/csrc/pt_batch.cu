@@ -98,7 +98,8 @@ int calibrate(pt_ctx* c, int tier, const HostDeBlock& b0, int model) {
   const HostDeBlock& b = b0;
   const int64_t nt = b.blk.ntiles;
   const double np = (double)npad_of(tier, b.pop);
-  const int S = pick_sc_tiles(c, tier, b.blk.esize, 96, model);
+  // the most tiles a CTA keeps resident (without the second trial set)
+  const int S = pick_sc_tiles(c, tier, b.blk.esize, 96, model, false);
   c->tune_res_tiles = S;
   // two resident shapes: about S/3 and 2S/3 tiles per CTA
   int ka = clamp_k(c, (nt + std::max(1, S / 3) - 1) / std::max(1, S / 3));

@@ -158,6 +158,7 @@ int kernel_status(pt_ctx* c, cudaStream_t s, int* d_err);
 size_t de_desc_bytes(int nblocks, int ngroups);
 
 // Staged tiles per CTA for a launch whose CTAs own at most `want` tiles.
-int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want, int model = HOST_MODEL_CUBIC);
+int pick_sc_tiles(pt_ctx* c, int tier, int esize_max, int64_t want, int model = HOST_MODEL_CUBIC,
+                  bool ahead = true);
 
 }  // namespace pt

@@ -722,14 +722,15 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 // npad: padded candidates; tmax: max tiles per CTA; cgv: candidates per item;
 // pop: population slots (0 for the objective kernel); nthreads: CTA size.
 // model: MODEL_CUBIC or MODEL_FULL (wider population rows, candidate data and anchors).
-// With pop > 0 (the DE): two generations' draws, and a second set of trials
-// and set-up (the next generation's, built ahead) with a flag per individual;
-// the current generation's set keeps fixed offsets ahead of them.
+// With pop > 0 (the DE): two generations' draws, and with `ahead` a second
+// set of trials and set-up (the next generation's, built ahead) with a flag
+// per individual; the current generation's set keeps fixed offsets ahead of
+// them.
 __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, int cgv, int esize, int pop,
-                                                  int nthreads, int model = MODEL_CUBIC) {
+                                                  int nthreads, int model = MODEL_CUBIC, bool ahead_set = true) {
   SmemLayout s;
   size_t o = 0;
-  const size_t ahead = pop ? 1 : 0;
+  const size_t ahead = (pop && ahead_set) ? 1 : 0;
   s.off_mbar = o;
   o += 16;
   s.off_pop = o;
@@ -868,6 +869,7 @@ struct DeLaunch {
   uint64_t timeout_ns;
   int obj;                   // OBJ_CHI2 or OBJ_COR (the kernel instantiation launched)
   uint32_t extra_tx;         // 0, or the bytes a test of the staging wait adds (bulk_stage)
+  int ahead;                 // the second trial set is laid out (every block of the launch is resident)
 };
 
 // One generation's draws: packed indices, crossover mask, model_dim jitter
@@ -1105,7 +1107,7 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
   // than warp 0 (none when rem = 0)
   const int rem = (ihi - ilo) % nw;
   const int first_early =
-      (resident && strat != DE_BEST1_JITTER && rem > 0 && nw - rem >= AHEAD_MIN_WARPS) ? rem : -1;
+      (a.ahead && resident && strat != DE_BEST1_JITTER && rem > 0 && nw - rem >= AHEAD_MIN_WARPS) ? rem : -1;
   if (resident && nt > 0 &&
       !stage_tiles<TIER>(b, tb, nt, sm.raw, sm.s32, sm.s64, sm.mbar, a.timeout_ns, a.err, a.extra_tx))
     return false;
@@ -1247,7 +1249,7 @@ template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC, int SK = -1>
 __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int DIM = model_dim(MODEL);
-  const SmemLayout S = smem_layout(TIER, NP_MAX, a.sc_tiles, 16, a.esize_max, NP_MAX, NT, MODEL);
+  const SmemLayout S = smem_layout(TIER, NP_MAX, a.sc_tiles, 16, a.esize_max, NP_MAX, NT, MODEL, a.ahead != 0);
   DeSmem sm;
   sm.mbar = reinterpret_cast<uint64_t*>(smem + S.off_mbar);
   sm.x = reinterpret_cast<double*>(smem + S.off_pop);
