@@ -722,10 +722,10 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 // npad: padded candidates; tmax: max tiles per CTA; cgv: candidates per item;
 // pop: population slots (0 for the objective kernel); nthreads: CTA size.
 // model: MODEL_CUBIC or MODEL_FULL (wider population rows, candidate data and anchors).
-// With pop > 0 (the DE): two generations' draws, and with `ahead` a second
-// set of trials and set-up (the next generation's, built ahead) with a flag
-// per individual; the current generation's set keeps fixed offsets ahead of
-// them.
+// With pop > 0 (the DE): two generations' draws, a replacement flag per
+// individual and, with `ahead_set`, a second set of trials and set-up (the
+// next generation's, built ahead); the current generation's set keeps fixed
+// offsets ahead of them.
 __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, int cgv, int esize, int pop,
                                                   int nthreads, int model = MODEL_CUBIC, bool ahead_set = true) {
   SmemLayout s;
@@ -758,8 +758,8 @@ __host__ __device__ inline SmemLayout smem_layout(int tier, int npad, int tmax, 
   o += ahead * align_up((size_t)npad * sizeof(int), 16);
   s.off_cub2 = o;
   o += ahead * align_up((size_t)npad, 16);
-  s.off_win = o;
-  o += ahead * align_up((size_t)npad, 16);
+  s.off_win = o;  // the replacement flags: every DE launch
+  o += (pop ? 1 : 0) * align_up((size_t)npad, 16);
   s.off_anc = o;
   o += (tier == TIER_F64) ? (size_t)(nthreads / 32) * IPB * cgv * anchor_words(model) * sizeof(uint4) : 0;
   s.off_samp = o;
