@@ -436,6 +436,7 @@ def run_gpu(args):
         torch.cuda.set_stream(torch.cuda.default_stream())
         mb = measure_batch(256, steps=1, warmup=1, e2e_steps=1)
         ms_ = measure_serve(args.serve_seconds, args.speedup, args.inflight)
+        mo = measure_objective(4096, steps=5, warmup=3)
         line["batch_blocks_per_s"] = mb["blocks_per_s"]
         line["plain_f64_blocks_per_s"] = mb["plain_blocks_per_s"]
         line["batch_over_plain_f64"] = mb["blocks_per_s"] / mb["plain_blocks_per_s"]
@@ -448,11 +449,18 @@ def run_gpu(args):
         line["serve_p99_over_real_block_duration"] = float(np.percentile(ms_["lat_real_rel"], 99))
         line["serve_blocks"] = ms_["n"]
         line["serve_status_ok"] = ms_["status_ok"]
+        line["objective_sample_evals_per_s"] = mo["achieved"]
+        line["objective_frac_of_sfu_peak"] = mo["achieved"] / peak
+        line["objective_sse_rel_err_vs_oracle_max"] = mo["sse_rel_err_max"]
+        line["objective_clocks"] = mo["clocks"]
         line["extras_config"] = {
             "batch": "256 blocks, N log-uniform 50K-1M int16, fs 1-50 kHz, pop 32-128, G = ceil(80000/pop); "
                      "one timed run after one warm-up, CUDA events, L2 flushed",
             "plain_f64": "all-FP64 tier, one pt_de_solve per block on the batch's quartile- and median-length "
                          "blocks, blocks/s extrapolated to the batch's sample-evals",
+            "objective": "pt_objective alone (k_objective<TIER_F64, 16>, Eq. 2-2-4): the 400K int16 block x 4096 "
+                         "candidates inside its bounds, device pointers, L2 flushed, 5 timed calls after 3 "
+                         "warm-up calls, by the library's kernel events; SSE of 8 of them against the oracle",
             "serve": f"4 streams (10/20/35/50 kHz, 1-10 s blocks), {args.serve_seconds:.0f} simulated s replayed "
                      f"{args.speedup:.0f}x faster than real time, pop 64, 1250 generations, warm-started; "
                      "latency from arrival to result; serve_p99_over_block_duration is against the compressed "
@@ -681,62 +689,76 @@ def run_serve(args):
     return 0
 
 
-def run_objective(args):
+def measure_objective(ncand: int, steps: int, warmup: int) -> dict:
     """The objective kernel alone (pt_objective, Eq. 2-2-4): the paper-size
-    400K int16 block against `--ncand` candidates drawn inside its bounds,
+    400K int16 block against `ncand` candidates drawn inside its bounds,
     candidates and results resident on the device (device pointers), L2
-    flushed between steps. Reports sample-evals/s against the SFU roofline."""
+    flushed between steps. Per-call CUDA-event times on the library's stream
+    and the library's own kernel times, the clocks during the timed calls,
+    and the SSE of sampled candidates against the oracle (after timing)."""
     import torch
     import paper_1906_10598_b300 as pt
-    from paper_1906_10598_b300 import build
-    build.build()
     blk = synth.paper400k(0)
     ctx = pt.Context(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx.set_stream(stream.cuda_stream)
-    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
-    rng = np.random.default_rng(0)
-    lo, hi = blk.bounds[:, 0], blk.bounds[:, 1]
-    cands = torch.tensor(lo + rng.random((args.ncand, 5)) * (hi - lo), dtype=torch.float64, device="cuda")
-    out = torch.empty(args.ncand, dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        ctx.objective(cands, pt.TIER_F64, out=out)
-    sampler = ClockSampler(0)
-    sampler.start()
-    ms, kms = [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.objective(cands, pt.TIER_F64, out=out)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        kms.append(ctx.last_kernel_ms())
-    clocks = sampler.stop()
-    evals = float(blk.n) * args.ncand
-    value = evals * args.steps / (float(np.sum(ms)) * 1e-3)
-    achieved = evals / (float(np.mean(kms)) * 1e-3)
+    try:
+        ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+        rng = np.random.default_rng(0)
+        lo, hi = blk.bounds[:, 0], blk.bounds[:, 1]
+        cands = torch.tensor(lo + rng.random((ncand, 5)) * (hi - lo), dtype=torch.float64, device="cuda")
+        out = torch.empty(ncand, dtype=torch.float64, device="cuda")
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        for _ in range(warmup):
+            ctx.objective(cands, pt.TIER_F64, out=out)
+        sampler = ClockSampler(0)
+        sampler.start()
+        ms, kms = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.objective(cands, pt.TIER_F64, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            kms.append(ctx.last_kernel_ms())
+        clocks = sampler.stop()
+        got = out.cpu().numpy()
+        idx = np.arange(0, ncand, max(1, ncand // 8))
+        host_cands = cands.cpu().numpy()[idx]
+    finally:
+        ctx.close()
+        torch.cuda.set_stream(torch.cuda.default_stream())
+    import oracle
+    want = oracle.sse_many(blk.values(), blk.fs, blk.t0, host_cands)
+    evals = float(blk.n) * ncand
+    return {"n": blk.n, "evals": evals, "ms": ms, "kernel_ms": kms, "clocks": clocks,
+            "value": evals * steps / (float(np.sum(ms)) * 1e-3), "achieved": evals / (float(np.mean(kms)) * 1e-3),
+            "sse_rel_err_max": float(np.max(np.abs(got[idx] - want) / want))}
+
+
+def run_objective(args):
+    """The objective kernel alone (measure_objective) as its own JSON line,
+    against the SFU roofline."""
+    from paper_1906_10598_b300 import build
+    build.build()
+    mo = measure_objective(args.ncand, args.steps, args.warmup)
     sfu = sfu_peak(measure_pipes(0, full=False))
     peak = sfu["peak"]
-    got = out.cpu().numpy()
-    idx = np.arange(0, args.ncand, max(1, args.ncand // 8))
-    import oracle
-    want = oracle.sse_many(blk.values(), blk.fs, blk.t0, cands.cpu().numpy()[idx])
-    line = {"metric": "objective kernel sample-evals/s", "value": value, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "paper400k_int16_objective", "n": blk.n, "candidates": args.ncand,
+    line = {"metric": "objective kernel sample-evals/s", "value": mo["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(mo["ms"])),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper400k_int16_objective", "n": mo["n"], "candidates": args.ncand,
                        "tier": "f64-anchored phase, f32 cos", "l2": "flushed between steps"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-                         "traffic": None, "kernel": "k_objective<TIER_F64, 16>", "peak_basis": sfu["basis"]},
-            "clocks": clocks, "gpu_launches": 2 * args.steps,
-            "sse_rel_err_vs_oracle_max": float(np.max(np.abs(got[idx] - want) / want))}
+            "roofline": {"bound": "alu", "achieved": mo["achieved"], "peak": peak, "unit": UNIT,
+                         "frac": mo["achieved"] / peak, "traffic": None, "kernel": "k_objective<TIER_F64, 16>",
+                         "peak_basis": sfu["basis"]},
+            "clocks": mo["clocks"], "gpu_launches": 2 * args.steps,
+            "sse_rel_err_vs_oracle_max": mo["sse_rel_err_max"]}
     print(json.dumps(line))
-    ctx.close()
     return 0
 
 
