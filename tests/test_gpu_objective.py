@@ -115,7 +115,7 @@ def test_ragged_and_tiny_blocks(ctx, n):
         bound = residual_term_bound(want, n, np.max(np.abs(s)), np.max(np.abs(cands[:, 0])))
         assert np.all(np.abs(got - want) <= bound), (sigma, np.abs(got - want), bound)
         if sigma == 0.3 and n >= 255:
-            # noisy blocks of a tile or more: the benchmark spec's 1e-6 alone
+            # noisy blocks of a tile or more: the 1e-6 relative bound alone
             assert np.max(_rel(got, want)) <= 1e-6, (sigma, _rel(got, want))
         plain = ctx.objective(cands, pt.TIER_PLAIN)
         assert np.max(_rel(plain, want)) <= 1e-9, _rel(plain, want)

@@ -6,7 +6,7 @@ tests/golden/precision_oracle_fits.json holds the FP64 oracle's own fits of
 these blocks, written by tests/golden/make_precision_oracle.py, which calls
 only the oracle and the input generators (each fit takes the oracle minutes
 of host time). The default tier's fit must agree with the oracle's within the
-spec tolerances (phi0 within 1e-3 rad, f0 within 1e-5 Hz) wherever the
+fit tolerances (phi0 within 1e-3 rad, f0 within 1e-5 Hz) wherever the
 oracle reached the global basin (its SSE at or below the truth's), and its
 SSE must match the oracle's evaluation of the same parameters within 1e-6.
 """

@@ -3,7 +3,8 @@ DE/rand/1 either-or algorithm) of Table 3-1-1 against the oracle.
 
 The draws and the FP64 trial arithmetic are the oracle's, so the populations
 agree bit for bit until a selection compares two objective values closer than
-the tier's error; the fits agree within the benchmark spec's tolerances.
+the tier's error; the fits agree within the fit tolerances (phi0 within
+1e-3 rad, f0 within 1e-5 Hz of the oracle's fit).
 """
 import math
 
