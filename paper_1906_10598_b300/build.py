@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libphasetrack.so")
 SOURCES = ["pt_api.cu", "pt_batch.cu", "pt_serve.cu", "pt_noalloc.cu", "pt_track.cu", "pt_seed.cu",
            "pt_pipes.cu"]
-DEPS = SOURCES + ["pt_kernels.cuh", "pt_device.cuh", "pt_internal.h"]
+DEPS = SOURCES + ["pt_kernels.cuh", "pt_device.cuh", "pt_internal.h", "pt_grid.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-shared",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "pt_grid.h"
 #include "pt_internal.h"
 #include "pt_kernels.cuh"
 
@@ -99,11 +100,10 @@ int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
   a.ncand = ncand;
   a.cpc = std::min(((ncand + CGV - 1) / CGV) * CGV, NP_MAX);
   const int ny = (ncand + a.cpc - 1) / a.cpc;
-  // about two CTAs per SM in total, tiles split evenly
-  const int64_t want = 2LL * c->sms;
-  int64_t tpc = (a.b.ntiles * ny + want - 1) / want;
-  tpc = std::max<int64_t>(1, std::min<int64_t>(tpc, 32));
-  a.tpc = (int)tpc;
+  // tiles split evenly, the grid sized to whole waves (objective_tiles_per_cta)
+  a.tpc = objective_tiles_per_cta(a.b.ntiles, ny, c->sms, [&](int t) {
+    return smem_layout(TIER, a.cpc, t, CGV, a.b.esize, 0, NT, MODEL).total <= c->smem_optin;
+  });
   const int nx = (int)((a.b.ntiles + a.tpc - 1) / a.tpc);
   a.acc = c->d_acc;
   a.err = c->d_err;

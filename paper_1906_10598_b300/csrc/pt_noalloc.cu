@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "../../include/phasetrack.h"
+#include "pt_grid.h"
 #include "pt_kernels.cuh"
 
 namespace {
@@ -106,8 +107,9 @@ int launch(const BlockArgs& b, const double* cands, int ncand, unsigned long lon
   a.ncand = ncand;
   a.cpc = std::min(((ncand + CGV - 1) / CGV) * CGV, NP_MAX);
   const int ny = (ncand + a.cpc - 1) / a.cpc;
-  const int64_t want = 2LL * sms;
-  a.tpc = (int)std::max<int64_t>(1, std::min<int64_t>((b.ntiles * ny + want - 1) / want, 32));
+  a.tpc = objective_tiles_per_cta(b.ntiles, ny, sms, [&](int t) {
+    return smem_layout(TIER, a.cpc, t, CGV, b.esize, 0, NT).total <= optin;
+  });
   const int nx = (int)((b.ntiles + a.tpc - 1) / a.tpc);
   a.acc = acc;
   a.err = err;
