@@ -138,6 +138,26 @@ def test_result_independent_of_batch_shape(ctx):
     assert np.array_equal(again, full)
 
 
+def test_whole_wave_grid_on_the_paper_block(ctx):
+    # The 400K block against 4096 candidates is the one launch whose grid
+    # takes more than 32 tiles per CTA (34: 1472 CTAs, whole waves of one CTA
+    # per SM). Its sums must equal, bit for bit, those of 128-candidate
+    # launches (6 tiles per CTA), and the oracle's within 1e-6.
+    import paper_1906_10598_b300 as pt
+    blk = synth.paper400k(0)
+    ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+    rng = np.random.default_rng(3)
+    lo, hi = blk.bounds[:, 0], blk.bounds[:, 1]
+    cands = lo + rng.random((4096, 5)) * (hi - lo)
+    full = ctx.objective(cands, pt.TIER_F64)
+    for k0 in (0, 1984, 3968):
+        part = ctx.objective(cands[k0:k0 + 128].copy(), pt.TIER_F64)
+        assert np.array_equal(part, full[k0:k0 + 128])
+    idx = np.arange(0, 4096, 256)
+    want = oracle.sse_many(blk.values(), blk.fs, blk.t0, cands[idx])
+    assert np.max(_rel(full[idx], want)) <= 1e-6
+
+
 def test_device_pointers_and_torch_stream(ctx):
     import torch
     import paper_1906_10598_b300 as pt
