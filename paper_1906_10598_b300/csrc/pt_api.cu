@@ -165,28 +165,36 @@ size_t smem_de(int tier, int sc_tiles, int esize_max, int model, bool ahead) {
   return smem_layout(tier, NP_MAX, sc_tiles, 16, esize_max, NP_MAX, NT, model, ahead).total;
 }
 
-template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC, int SK = -1>
+template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC, int SK = -1, int CGK = 0>
 int launch_de_t(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
   const size_t smem = smem_de(TIER, a.sc_tiles, a.esize_max, MODEL, a.ahead != 0);
   cudaFuncAttributes fa{};
-  PT_CUDA(c, cudaFuncGetAttributes(&fa, k_de<TIER, OBJ, MODEL, SK>));
+  PT_CUDA(c, cudaFuncGetAttributes(&fa, k_de<TIER, OBJ, MODEL, SK, CGK>));
   if (smem + fa.sharedSizeBytes > c->smem_optin) return fail(c, PT_EINVAL, "DE launch needs too much shared memory");
-  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, OBJ, MODEL, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PT_CUDA(c, cudaFuncSetAttribute(k_de<TIER, OBJ, MODEL, SK, CGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, OBJ, MODEL, SK>, NT, smem));
+  PT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_de<TIER, OBJ, MODEL, SK, CGK>, NT, smem));
   // pt_inject_missing_cta: the last group's last rank is not started, so its
   // arrivals never come and the others' bounded waits run out
   const int grid = a.ngroups * a.k - (c->inject_missing_cta && a.ngroups * a.k > 1 ? 1 : 0);
   if (occ < 1 || grid > occ * c->sms) return fail(c, PT_EINVAL, "DE grid cannot be co-resident");
   void* args[] = {&a};
-  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, OBJ, MODEL, SK>, dim3(grid), dim3(NT), args, smem, s));
+  PT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_de<TIER, OBJ, MODEL, SK, CGK>, dim3(grid), dim3(NT), args, smem, s));
   return PT_OK;
 }
 
 // The default tier's DE kernels are compiled per strategy (every block of a
-// launch has the context's strategy).
+// launch has the context's strategy), and once more for launches whose blocks
+// all evaluate 16-candidate items on resident tiles (cg16 and a.ahead).
 template <int OBJ, int MODEL = MODEL_CUBIC>
-int launch_de_f64(pt_ctx* c, cudaStream_t s, DeLaunch& a) {
+int launch_de_f64(pt_ctx* c, cudaStream_t s, DeLaunch& a, bool cg16) {
+  if (cg16 && a.ahead) {
+    switch (c->strategy) {
+      case DE_BEST1_JITTER: return launch_de_t<TIER_F64, OBJ, MODEL, DE_BEST1_JITTER, 16>(c, s, a);
+      case DE_EITHER_OR: return launch_de_t<TIER_F64, OBJ, MODEL, DE_EITHER_OR, 16>(c, s, a);
+      default: return launch_de_t<TIER_F64, OBJ, MODEL, DE_RAND1_BIN, 16>(c, s, a);
+    }
+  }
   switch (c->strategy) {
     case DE_BEST1_JITTER: return launch_de_t<TIER_F64, OBJ, MODEL, DE_BEST1_JITTER>(c, s, a);
     case DE_EITHER_OR: return launch_de_t<TIER_F64, OBJ, MODEL, DE_EITHER_OR>(c, s, a);
@@ -276,6 +284,7 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   // the arrival count of a ring word is its low byte (de_block): k <= 255
   if (k < 1 || k > HOST_DE_GROUP_MAX) return fail(c, PT_EINVAL, "DE group size must be 1 .. 255 CTAs");
   std::vector<DeBlockDesc> desc(nblocks);
+  bool cg16 = true;  // every block evaluates 16-candidate items
   int esize_max = 1;
   int64_t want = 1;
   for (int i = 0; i < nblocks; ++i) {
@@ -297,6 +306,7 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
     d.np = h.pop;
     d.gens = h.gens;
     d.cg = pick_cg(tier, h.pop);
+    cg16 = cg16 && d.cg == 16;
     d.out = h.out;
     d.pop_out = h.pop_out;
     d.fit_out = h.fit_out;
@@ -335,7 +345,7 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
     // the full model: the chi-square (checked by the entry points)
     a.obj = OBJ_CHI2;
     switch (tier) {
-      case PT_TIER_F64: return launch_de_f64<OBJ_CHI2, MODEL_FULL>(c, s, a);
+      case PT_TIER_F64: return launch_de_f64<OBJ_CHI2, MODEL_FULL>(c, s, a, cg16);
       case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN, OBJ_CHI2, MODEL_FULL>(c, s, a);
       case PT_TIER_DF32: return launch_de_t<TIER_DF32, OBJ_CHI2, MODEL_FULL>(c, s, a);
       default: return launch_de_t<TIER_F32, OBJ_CHI2, MODEL_FULL>(c, s, a);
@@ -344,14 +354,14 @@ int launch_de_groups(pt_ctx* c, cudaStream_t s, int tier, const HostDeBlock* blo
   a.obj = c->objective;
   if (a.obj == OBJ_COR) {
     switch (tier) {
-      case PT_TIER_F64: return launch_de_f64<OBJ_COR>(c, s, a);
+      case PT_TIER_F64: return launch_de_f64<OBJ_COR>(c, s, a, cg16);
       case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN, OBJ_COR>(c, s, a);
       case PT_TIER_DF32: return launch_de_t<TIER_DF32, OBJ_COR>(c, s, a);
       default: return launch_de_t<TIER_F32, OBJ_COR>(c, s, a);
     }
   }
   switch (tier) {
-    case PT_TIER_F64: return launch_de_f64<OBJ_CHI2>(c, s, a);
+    case PT_TIER_F64: return launch_de_f64<OBJ_CHI2>(c, s, a, cg16);
     case PT_TIER_PLAIN: return launch_de_t<TIER_PLAIN>(c, s, a);
     case PT_TIER_DF32: return launch_de_t<TIER_DF32>(c, s, a);
     default: return launch_de_t<TIER_F32>(c, s, a);

@@ -53,6 +53,7 @@ constexpr float TWO_PI_2M64 = 3.40612158008655460e-19f;
 // Status written by a kernel into its error word (0 = OK).
 constexpr int DEV_OK = 0;
 constexpr int DEV_TIMEOUT = 1;   // a bounded wait expired
+constexpr int DEV_LAYOUT = 2;    // a CTA's tiles exceed the resident layout its kernel was compiled for
 
 // Per-block constants shared by all kernels.
 struct BlockArgs {

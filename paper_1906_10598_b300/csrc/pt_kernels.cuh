@@ -1083,7 +1083,7 @@ __device__ __forceinline__ void take_ahead_setup(const DeSmem& sm, int np, int n
 // another CTA failed.
 // MODEL_FULL: the full model's 7 parameters (chi-square).
 // SK: the launch's strategy when fixed at compile time, -1 to read it from the block.
-template <int TIER, int CGV, int OBJ, int MODEL = MODEL_CUBIC, int SK = -1>
+template <int TIER, int CGV, int OBJ, int MODEL = MODEL_CUBIC, int SK = -1, bool STREAM = true>
 __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long long* ring, unsigned long long& gg,
                          const DeSmem& sm, const DeLaunch& a, int* s_abort, int* s_nrep) {
   constexpr int DIM = model_dim(MODEL);
@@ -1145,7 +1145,7 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
     } else if (resident) {
       eval_range<TIER, CGV, OBJ, MODEL>(b, tb, ilo, ihi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np, npad,
                                         sm.anc, sm.acc);
-    } else {
+    } else if constexpr (STREAM) {
       for (int c0 = 0; c0 < nt; c0 += a.sc_tiles) {
         const int cn = min(a.sc_tiles, nt - c0);
         const int lo = max(ilo, c0 * G) - c0 * G, hi = min(ihi, (c0 + cn) * G) - c0 * G;
@@ -1154,6 +1154,11 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
         eval_range<TIER, CGV, OBJ, MODEL>(b, tb + c0, lo, hi, sm.s32, sm.s64, sm.cdata, sm.negA, sm.kexp, sm.cub, np,
                                           npad, sm.anc, sm.acc);
       }
+    } else {
+      // compiled for resident tiles only: the launcher picks this kernel when
+      // every CTA's share fits, so this is a launcher error, reported
+      atomicExch(a.err, DEV_LAYOUT);
+      return false;
     }
     ahead = build_next;
     if (tid < np) {
@@ -1244,8 +1249,10 @@ __device__ bool de_block(const DeBlockDesc& d, int rank, int k, unsigned long lo
 // Launched cooperatively: the k CTAs of a group wait on one another. OBJ
 // selects the objective every block of the launch minimises; SK, when not -1,
 // the DE strategy of all its blocks (each strategy's kernel then holds only
-// its own trial code).
-template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC, int SK = -1>
+// its own trial code). CGK = 16, with SK: every block of the launch evaluates
+// 16-candidate items on resident tiles, so the kernel holds that one form of
+// the evaluation (no other item width, no streaming of tiles).
+template <int TIER, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC, int SK = -1, int CGK = 0>
 __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int DIM = model_dim(MODEL);
@@ -1291,7 +1298,9 @@ __global__ void __launch_bounds__(NT, 1) k_de(DeLaunch a) {
     __syncthreads();
     const DeBlockDesc& d = s_desc;
     bool ok;
-    if (TIER == TIER_F64 && d.cg == 16)
+    if constexpr (CGK == 16)
+      ok = de_block<TIER, 16, OBJ, MODEL, SK, false>(d, rank, a.k, ring, gg, sm, a, &s_abort, s_nrep);
+    else if (TIER == TIER_F64 && d.cg == 16)
       ok = de_block<TIER, 16, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort, s_nrep);
     else if (TIER == TIER_F64 && d.cg == 4)
       ok = de_block<TIER, 4, OBJ, MODEL, SK>(d, rank, a.k, ring, gg, sm, a, &s_abort, s_nrep);
