@@ -101,20 +101,20 @@ int launch_objective(pt_ctx* c, const double* d_cands, int ncand) {
   a.cpc = std::min(((ncand + CGV - 1) / CGV) * CGV, NP_MAX);
   const int ny = (ncand + a.cpc - 1) / a.cpc;
   // tiles split evenly, the grid sized to whole waves (objective_tiles_per_cta)
-  a.tpc = objective_tiles_per_cta(a.b.ntiles, ny, c->sms, [&](int t) {
-    return smem_layout(TIER, a.cpc, t, CGV, a.b.esize, 0, NT, MODEL).total <= c->smem_optin;
+  a.tpc = objective_tiles_per_cta(a.b.ntiles, ny, OBJ_CTAS * c->sms, [&](int t) {
+    return OBJ_CTAS * smem_layout(TIER, a.cpc, t, CGV, a.b.esize, 0, NT_OBJ, MODEL).total <= c->smem_optin;
   });
   const int nx = (int)((a.b.ntiles + a.tpc - 1) / a.tpc);
   a.acc = c->d_acc;
   a.err = c->d_err;
   a.timeout_ns = c->timeout_ns;
   a.extra_tx = c->inject_short_tx ? 16u : 0u;
-  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, a.b.esize, 0, NT, MODEL);
+  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, a.b.esize, 0, NT_OBJ, MODEL);
   if (S.total > c->smem_optin) return fail(c, PT_EINVAL, "objective launch needs too much shared memory");
   PT_CUDA(c, cudaFuncSetAttribute(k_objective<TIER, CGV, OBJ, MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)S.total));
   dim3 grid(nx, ny);
-  k_objective<TIER, CGV, OBJ, MODEL><<<grid, NT, S.total, c->stream>>>(a);
+  k_objective<TIER, CGV, OBJ, MODEL><<<grid, NT_OBJ, S.total, c->stream>>>(a);
   PT_CUDA(c, cudaGetLastError());
   return PT_OK;
 }

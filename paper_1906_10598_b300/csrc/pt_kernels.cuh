@@ -20,7 +20,9 @@
 
 namespace pt {
 
-constexpr int NT = 512;        // threads per CTA of the objective / DE kernels
+constexpr int NT = 512;        // threads per CTA of the DE kernels
+constexpr int NT_OBJ = 256;    // threads per CTA of the objective kernel, OBJ_CTAS of them per SM
+constexpr int OBJ_CTAS = 2;
 constexpr int CAND_BYTES = 64; // per-candidate prepared data in shared memory
 // The full model's per-candidate data: E0..E4 (5 x 16 B), then A0 and a1h (FP32).
 constexpr int CAND_BYTES_FULL = 96;
@@ -793,7 +795,7 @@ struct ObjArgs {
 };
 
 template <int TIER, int CGV, int OBJ = OBJ_CHI2, int MODEL = MODEL_CUBIC>
-__global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
+__global__ void __launch_bounds__(NT_OBJ, OBJ_CTAS) k_objective(ObjArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int64_t tb = (int64_t)blockIdx.x * a.tpc;
   const int nt = (int)min((int64_t)a.tpc, a.b.ntiles - tb);
@@ -801,7 +803,7 @@ __global__ void __launch_bounds__(NT, 1) k_objective(ObjArgs a) {
   const int nc = min(a.cpc, a.ncand - cb);
   if (nt <= 0 || nc <= 0) return;
   const int npad = (nc + CGV - 1) / CGV * CGV;
-  const SmemLayout S = smem_layout(TIER, npad, a.tpc, CGV, a.b.esize, 0, NT, MODEL);
+  const SmemLayout S = smem_layout(TIER, npad, a.tpc, CGV, a.b.esize, 0, NT_OBJ, MODEL);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S.off_mbar);
   unsigned char* cdata = smem + S.off_cdata;
   float* negA = reinterpret_cast<float*>(smem + S.off_negA);

@@ -107,19 +107,19 @@ int launch(const BlockArgs& b, const double* cands, int ncand, unsigned long lon
   a.ncand = ncand;
   a.cpc = std::min(((ncand + CGV - 1) / CGV) * CGV, NP_MAX);
   const int ny = (ncand + a.cpc - 1) / a.cpc;
-  a.tpc = objective_tiles_per_cta(b.ntiles, ny, sms, [&](int t) {
-    return smem_layout(TIER, a.cpc, t, CGV, b.esize, 0, NT).total <= optin;
+  a.tpc = objective_tiles_per_cta(b.ntiles, ny, OBJ_CTAS * sms, [&](int t) {
+    return OBJ_CTAS * smem_layout(TIER, a.cpc, t, CGV, b.esize, 0, NT_OBJ).total <= optin;
   });
   const int nx = (int)((b.ntiles + a.tpc - 1) / a.tpc);
   a.acc = acc;
   a.err = err;
   a.timeout_ns = 2000000000ull;
-  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, b.esize, 0, NT);
+  const SmemLayout S = smem_layout(TIER, a.cpc, a.tpc, CGV, b.esize, 0, NT_OBJ);
   if (S.total > optin) return PT_EINVAL;
   if (cudaFuncSetAttribute(k_objective<TIER, CGV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total) !=
       cudaSuccess)
     return PT_ECUDA;
-  k_objective<TIER, CGV><<<dim3(nx, ny), NT, S.total, s>>>(a);
+  k_objective<TIER, CGV><<<dim3(nx, ny), NT_OBJ, S.total, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? PT_OK : PT_ECUDA;
 }
 
