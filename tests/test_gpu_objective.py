@@ -140,9 +140,9 @@ def test_result_independent_of_batch_shape(ctx):
 
 def test_whole_wave_grid_on_the_paper_block(ctx):
     # The 400K block against 4096 candidates is the one launch whose grid
-    # takes more than 32 tiles per CTA (34: 1472 CTAs, whole waves of one CTA
-    # per SM). Its sums must equal, bit for bit, those of 128-candidate
-    # launches (6 tiles per CTA), and the oracle's within 1e-6.
+    # takes more than 32 tiles per CTA (34: 1472 CTAs, whole waves of two
+    # CTAs per SM). Its sums must equal, bit for bit, those of 128-candidate
+    # launches (3 tiles per CTA), and the oracle's within 1e-6.
     import paper_1906_10598_b300 as pt
     blk = synth.paper400k(0)
     ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
