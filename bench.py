@@ -378,12 +378,14 @@ def run_gpu(args):
     total_ms = replicas.max_over_ranks(total_ms, device="cuda")
 
     # end to end through the C ABI with host buffers: H2D of the step's samples
-    # (pt_load_block) + the fit + D2H of the result, every step
+    # (pt_load_block, from pinned host memory) + the fit + D2H of the result,
+    # every step
+    host_samples = torch.from_numpy(blk.samples).pin_memory().numpy()
     e2e_s = []
     for _ in range(max(3, args.steps // 2)):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        ctx.load_block(blk.samples, blk.fs, blk.t0, blk.scale)
+        ctx.load_block(host_samples, blk.fs, blk.t0, blk.scale)
         step()
         e2e_s.append(time.perf_counter() - t)
     e2e_v = evals * world / replicas.max_over_ranks(float(np.mean(e2e_s)), device="cuda")
@@ -529,7 +531,10 @@ def measure_batch(nblocks: int, steps: int, warmup: int, full: bool = False, e2e
         fast_s += ctx.last_kernel_ms() * 1e-3
         plain_evals += b.sample_evals()
     plain_rate = plain_evals / plain_s
-    # end to end: fresh batch every step (H2D of every block's samples, launch, results)
+    # end to end: fresh batch every step (H2D of every block's samples from
+    # pinned host memory, launch, results)
+    for b in blocks:
+        b.samples = torch.from_numpy(b.samples).pin_memory().numpy()
     e2e = []
     for _ in range(max(1, e2e_steps)):
         torch.cuda.synchronize()
